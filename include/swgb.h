@@ -1,0 +1,179 @@
+/*
+ * swgb.h -- C ABI of the GB300 (sm_103a) exact affine-gap Smith-Waterman library.
+ *
+ * Method: Korpar & Sikic, "SW# - GPU enabled exact alignments on genome scale".
+ *   Sec. 2, wavefront paragraph    forward local pass -> best score S and end point
+ *   Sec. 2, pruning paragraph      cells that cannot reach the running best are skipped
+ *   Sec. 2, start-point paragraph  reverse pass from the end point, borders at -inf,
+ *                                  no zero floor -> start point
+ *   Sec. 2, reconstruction para.   linear-space divide and conquer between start and
+ *                                  end point -> the alignment
+ *
+ * Scoring.  Rows index sequence A (length n), columns sequence B (length m).
+ *   H[i][j] = max(0, H[i-1][j-1] + s(a_i, b_j), E[i][j], F[i][j])
+ *   E[i][j] = max(E[i][j-1] - ge, H[i][j-1] - go)      (horizontal gap, consumes B)
+ *   F[i][j] = max(F[i-1][j] - ge, H[i-1][j] - go)      (vertical gap, consumes A)
+ *   so a gap of length k costs go + ge*(k-1)  (the paper's affine model).
+ *
+ * Results are exact and deterministic (the paper fixes no tie rule; these are the
+ * library's):
+ *   end point   first cell with H = S in row-major order of (A, B);
+ *   start point among cells of the reverse pass reaching S, the first in row-major
+ *               order of the reversed sequences (the largest start, shortest alignment);
+ *   alignment   greedy traceback from the end point: at a full cell diagonal >
+ *               vertical (I) > horizontal (D); inside a gap, open > extend.
+ *   Coordinates are 0-based, end exclusive.  S = 0 gives score 0, coordinates -1
+ *   and an empty CIGAR.
+ *
+ * CIGAR ops: '=' identical codes, 'X' different codes, 'I' consumes A only,
+ * 'D' consumes B only; runs are written as <length><op>.
+ *
+ * Memory.  Every call runs on the context's CUDA stream and takes its device
+ * scratch (boundary rows, band flags, checkpoint rows) from the context's
+ * workspace, a caller-provided device buffer or one the context allocated.
+ * Host buffers passed in are read before the call returns; device buffers
+ * (SW_FLAG_DEVICE_INPUT) must stay valid until it returns.
+ *
+ * Errors.  Every entry point returns an sw_status; nothing is thrown across the
+ * ABI.  SW_ECUDA leaves the reason in sw_ctx_last_error().  SW_ETIMEOUT means an
+ * inter-band wait inside a kernel ran past its limit: the kernel stopped itself
+ * and the context remains usable.
+ *
+ * Threading.  A context may be used by one host thread at a time.
+ */
+#ifndef SWGB_H
+#define SWGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SW_OK = 0,
+    SW_EINVAL = 1,     /* bad argument: lengths, codes >= alphabet, scheme out of range */
+    SW_ENOMEM = 2,     /* workspace too small for this call (or host allocation failed) */
+    SW_ECUDA = 3,      /* CUDA runtime error; see sw_ctx_last_error() */
+    SW_ETIMEOUT = 4,   /* a bounded device-side wait expired */
+    SW_EBUSY = 5,      /* serving: request refused by admission (memory budget / slots) */
+    SW_ENOTIMPL = 6,
+    SW_EPENDING = 7    /* serving: result not ready yet */
+} sw_status;
+
+/* call flags */
+#define SW_FLAG_DEVICE_INPUT  0x1   /* a, b are device pointers (else host) */
+#define SW_FLAG_SCORE_ONLY    0x2   /* batch / serving: score and end point only */
+#define SW_FLAG_NO_PRUNE      0x4   /* disable block pruning (results are identical) */
+#define SW_FLAG_FORCE_INT32   0x8   /* batch: never use int16x2 lanes */
+#define SW_FLAG_FORCE_INT16   0x10  /* batch: int16x2 lanes even when the static bound
+                                       does not rule out overflow (overflow is detected
+                                       and the pair re-run in int32) */
+
+/* Substitution scores and gap costs.  Codes are 0..alphabet-1 (DNA: A0 C1 G2 T3,
+ * N4).  matrix == NULL uses match on identical codes below 4 and mismatch
+ * elsewhere (so N mismatches everything).  Limits: 1 <= alphabet <= 8, scores in
+ * [-127, 127], gap_open >= gap_extend >= 1, gap_open <= 65535. */
+typedef struct {
+    int32_t alphabet;
+    const int8_t *matrix;       /* host, alphabet*alphabet row-major, or NULL */
+    int32_t match, mismatch;
+    int32_t gap_open, gap_extend;
+} sw_scheme;
+
+typedef struct {
+    int64_t cells;             /* n*m of the forward pass */
+    int64_t cells_computed;    /* cells actually computed by all passes */
+    int64_t tiles_total;       /* forward-pass 32-column band tiles */
+    int64_t tiles_pruned;      /* of which skipped by the pruning bound */
+    int32_t int16_reruns;      /* batch: pairs re-run in int32 after int16 overflow */
+    int32_t levels;            /* reconstruction: divide-and-conquer levels */
+    float ms_forward, ms_start, ms_align;   /* device time per phase */
+} sw_stats;
+
+typedef struct {
+    int64_t score;
+    int64_t a_begin, a_end, b_begin, b_end;   /* -1 when score == 0 or score-only start */
+    char *cigar;                              /* library-owned; free with sw_result_free */
+    int64_t cigar_len;
+    sw_stats stats;
+} sw_result;
+
+typedef struct {
+    const uint8_t *a; int64_t n;
+    const uint8_t *b; int64_t m;
+} sw_pair;
+
+typedef struct sw_ctx sw_ctx;
+
+/* Create a context on `device` using CUDA stream `stream` (cudaStream_t, NULL =
+ * legacy default stream).  `workspace` is a device buffer of `workspace_bytes`
+ * that the library sub-allocates and never frees (the caller owns it); pass
+ * NULL to let the context cudaMalloc `workspace_bytes` itself (freed by
+ * sw_ctx_destroy).  Returns SW_EINVAL, SW_ECUDA or SW_OK. */
+int sw_ctx_create(int device, void *stream, void *workspace, uint64_t workspace_bytes,
+                  sw_ctx **out);
+void sw_ctx_destroy(sw_ctx *ctx);
+const char *sw_ctx_last_error(const sw_ctx *ctx);
+const char *sw_strerror(int status);
+
+/* Tuning / testing knobs (values persist on the context):
+ *   SW_OPT_ROWS_PER_THREAD  forward pass rows per thread: 8, 16, 24 or 32
+ *   SW_OPT_WARPS_PER_SM     resident warps per SM for the persistent kernels
+ *   SW_OPT_TIMEOUT_MS       limit of every device-side inter-band wait
+ *   SW_OPT_FAULT_BAND       testing: this forward-pass band never publishes its
+ *                           progress (-1 = off), so the next band's bounded wait
+ *                           expires and the call returns SW_ETIMEOUT
+ *   SW_OPT_CKPT_BANDS       reconstruction: bands between checkpoint rows at level 0
+ *   SW_OPT_LEAF_CELLS       reconstruction: largest sub-problem solved by full traceback */
+enum {
+    SW_OPT_ROWS_PER_THREAD = 1,
+    SW_OPT_WARPS_PER_SM = 2,
+    SW_OPT_TIMEOUT_MS = 3,
+    SW_OPT_FAULT_BAND = 4,
+    SW_OPT_CKPT_BANDS = 5,
+    SW_OPT_LEAF_CELLS = 6
+};
+int sw_ctx_set_option(sw_ctx *ctx, int option, int64_t value);
+
+/* Score and end point (Sec. 2, wavefront and pruning paragraphs).  a[0..n),
+ * b[0..m) are codes below scheme->alphabet, host memory unless
+ * SW_FLAG_DEVICE_INPUT.  Fills score, a_end, b_end; a_begin = b_begin = -1;
+ * cigar = NULL.  n, m up to 2^31-1 (and max score * min(n, m) < 2^30). */
+int sw_score(sw_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64_t m,
+             const sw_scheme *scheme, int32_t flags, sw_result *out);
+
+/* Full alignment: score + end point, start point (Sec. 2, start-point paragraph)
+ * and the canonical alignment as a CIGAR (Sec. 2, reconstruction paragraph),
+ * in device memory linear in n + m plus the checkpoint rows.  The CIGAR is
+ * allocated by the library: release it with sw_result_free. */
+int sw_align(sw_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64_t m,
+             const sw_scheme *scheme, int32_t flags, sw_result *out);
+
+/* Many independent pairs in one persistent launch (device work queue over all
+ * pairs' row bands).  outs[count] receives one result per pair, in input order.
+ * With SW_FLAG_SCORE_ONLY only score and end point are produced; otherwise each
+ * pair is also aligned.  Pairs whose score bound fits int16 run on int16x2
+ * lanes unless SW_FLAG_FORCE_INT32. */
+int sw_align_batch(sw_ctx *ctx, const sw_pair *pairs, int32_t count,
+                   const sw_scheme *scheme, int32_t flags, sw_result *outs);
+
+/* The plain GPU path used as the comparison baseline: one thread per cell of
+ * each anti-diagonal, int32, no pruning, one launch per anti-diagonal.  Same
+ * score and end point as sw_score. */
+int sw_score_plain(sw_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64_t m,
+                   const sw_scheme *scheme, int32_t flags, sw_result *out);
+
+void sw_result_free(sw_result *r);
+
+/* Diagnostics: measured issue rate of one instruction kind on `device`, in
+ * 32-bit lane operations per SM clock (independent chains, full occupancy):
+ * kind 0 IADD, 1 IMNMX, 2 DPX viaddmax, 3 DPX viaddmax relu, 4 PRMT,
+ * 5 DPX viaddmax 16x2, 6 the forward pass's per-cell mix (8 ops per cell).
+ * Used for the forward pass's issue-rate roofline; allocates its own buffers. */
+int sw_probe_issue_rate(int device, int kind, double *ops_per_clk_per_sm);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWGB_H */

@@ -1,0 +1,256 @@
+"""Python binding of libswgb (include/swgb.h): argument marshalling only.
+
+Exact affine-gap Smith-Waterman on one GB300 (sm_103a): score and end point,
+start point and the canonical alignment (Korpar & Sikic, SW#, Sec. 2).  Every
+step runs in the library's CUDA kernels; this module only converts arguments.
+PyTorch supplies the device workspace and the CUDA stream.
+
+    import paper_1304_5966_gb300 as sw
+    ctx = sw.sw_ctx_create(workspace_bytes=1 << 30)
+    r = sw.sw_score(ctx, a, b)          # a, b: uint8 codes (numpy = host, torch cuda = device)
+    r = sw.sw_align(ctx, a, b)          # r.score, r.a_begin, ..., r.cigar
+
+There is no CPU fallback: if the shared library has not been built (see
+``build.py``) importing the binding's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libswgb.so")
+
+SW_OK, SW_EINVAL, SW_ENOMEM, SW_ECUDA, SW_ETIMEOUT, SW_EBUSY, SW_ENOTIMPL, SW_EPENDING = range(8)
+SW_FLAG_DEVICE_INPUT = 0x1
+SW_FLAG_SCORE_ONLY = 0x2
+SW_FLAG_NO_PRUNE = 0x4
+SW_FLAG_FORCE_INT32 = 0x8
+SW_FLAG_FORCE_INT16 = 0x10
+SW_OPT_ROWS_PER_THREAD, SW_OPT_WARPS_PER_SM, SW_OPT_TIMEOUT_MS, SW_OPT_FAULT_BAND, \
+    SW_OPT_CKPT_BANDS, SW_OPT_LEAF_CELLS = range(1, 7)
+
+
+class SwError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class _Scheme(ctypes.Structure):
+    _fields_ = [("alphabet", ctypes.c_int32), ("matrix", ctypes.c_void_p),
+                ("match", ctypes.c_int32), ("mismatch", ctypes.c_int32),
+                ("gap_open", ctypes.c_int32), ("gap_extend", ctypes.c_int32)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("cells", ctypes.c_int64), ("cells_computed", ctypes.c_int64),
+                ("tiles_total", ctypes.c_int64), ("tiles_pruned", ctypes.c_int64),
+                ("int16_reruns", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("ms_forward", ctypes.c_float), ("ms_start", ctypes.c_float),
+                ("ms_align", ctypes.c_float)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("score", ctypes.c_int64), ("a_begin", ctypes.c_int64), ("a_end", ctypes.c_int64),
+                ("b_begin", ctypes.c_int64), ("b_end", ctypes.c_int64),
+                ("cigar", ctypes.c_void_p), ("cigar_len", ctypes.c_int64), ("stats", _Stats)]
+
+
+class _Pair(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("b", ctypes.c_void_p), ("m", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libswgb; raises if it was not built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"libswgb not built ({_LIB_PATH}); run paper_1304_5966_gb300/build.py")
+        L = ctypes.CDLL(_LIB_PATH)
+        P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        L.sw_ctx_create.argtypes = [ctypes.c_int, P, P, ctypes.c_uint64, ctypes.POINTER(P)]
+        L.sw_ctx_destroy.argtypes = [P]
+        L.sw_ctx_destroy.restype = None
+        L.sw_ctx_last_error.argtypes = [P]
+        L.sw_ctx_last_error.restype = ctypes.c_char_p
+        L.sw_strerror.argtypes = [ctypes.c_int]
+        L.sw_strerror.restype = ctypes.c_char_p
+        L.sw_ctx_set_option.argtypes = [P, ctypes.c_int, i64]
+        for fn in ("sw_score", "sw_align", "sw_score_plain"):
+            getattr(L, fn).argtypes = [P, P, i64, P, i64, ctypes.POINTER(_Scheme), i32,
+                                       ctypes.POINTER(_Result)]
+        L.sw_align_batch.argtypes = [P, ctypes.POINTER(_Pair), i32, ctypes.POINTER(_Scheme), i32,
+                                     ctypes.POINTER(_Result)]
+        L.sw_result_free.argtypes = [ctypes.POINTER(_Result)]
+        L.sw_result_free.restype = None
+        _lib = L
+    return _lib
+
+
+@dataclass
+class Scheme:
+    """Substitution scores and affine gap costs (gap of length k = go + ge*(k-1))."""
+    match: int = 1
+    mismatch: int = -3
+    gap_open: int = 5
+    gap_extend: int = 2
+    alphabet: int = 4
+    matrix: tuple | None = None
+
+    def _c(self):
+        s = _Scheme(self.alphabet, None, self.match, self.mismatch, self.gap_open, self.gap_extend)
+        keep = None
+        if self.matrix is not None:
+            keep = np.ascontiguousarray(np.asarray(self.matrix, dtype=np.int8))
+            s.matrix = keep.ctypes.data
+        return s, keep
+
+
+DNA = Scheme()
+
+
+@dataclass
+class Result:
+    score: int
+    a_begin: int
+    a_end: int
+    b_begin: int
+    b_end: int
+    cigar: str | None
+    stats: dict = field(default_factory=dict)
+
+
+class Context:
+    """A library context: device, CUDA stream and a device workspace from torch."""
+
+    def __init__(self, device: int = 0, workspace_bytes: int = 1 << 30, stream=None, workspace=None):
+        import torch
+        self.device = device
+        torch.cuda.set_device(device)
+        if workspace is None:
+            workspace = torch.empty(int(workspace_bytes), dtype=torch.uint8, device=f"cuda:{device}")
+        self.workspace = workspace            # kept alive for the context's lifetime
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = ctypes.c_void_p()
+        st = lib().sw_ctx_create(device, ctypes.c_void_p(self.stream.cuda_stream),
+                                 ctypes.c_void_p(workspace.data_ptr()),
+                                 workspace.numel() * workspace.element_size(), ctypes.byref(h))
+        if st != SW_OK:
+            raise SwError(st, "sw_ctx_create failed: " + lib().sw_strerror(st).decode())
+        self.handle = h
+
+    def set_option(self, option: int, value: int):
+        _check(self, lib().sw_ctx_set_option(self.handle, option, int(value)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sw_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return lib().sw_ctx_last_error(self.handle).decode()
+
+
+def sw_ctx_create(device: int = 0, workspace_bytes: int = 1 << 30, stream=None, workspace=None) -> Context:
+    return Context(device, workspace_bytes, stream, workspace)
+
+
+def sw_ctx_destroy(ctx: Context):
+    ctx.close()
+
+
+def _check(ctx, st):
+    if st != SW_OK:
+        raise SwError(st, f"{lib().sw_strerror(st).decode()}: {ctx.last_error()}")
+
+
+def _seq(x):
+    """(pointer, length, is_device, keepalive) for a numpy/bytes/torch sequence of codes."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if x.dtype != torch.uint8 or not x.is_contiguous():
+                raise TypeError("device sequences must be contiguous torch.uint8")
+            return x.data_ptr(), x.numel(), x.is_cuda, x
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(np.asarray(x, dtype=np.uint8))
+    return arr.ctypes.data, len(arr), False, arr
+
+
+def _result(r: _Result) -> Result:
+    cig = None
+    if r.cigar:
+        cig = ctypes.string_at(r.cigar, r.cigar_len).decode()
+    st = {f: getattr(r.stats, f) for f, _ in _Stats._fields_}
+    return Result(int(r.score), int(r.a_begin), int(r.a_end), int(r.b_begin), int(r.b_end), cig, st)
+
+
+def _pairwise(fn, ctx, a, b, scheme, flags):
+    pa, n, da, ka = _seq(a)
+    pb, m, db, kb = _seq(b)
+    if da != db:
+        raise ValueError("a and b must both be host or both be device sequences")
+    if da:
+        flags |= SW_FLAG_DEVICE_INPUT
+    sch, keep = (scheme or DNA)._c()
+    res = _Result()
+    st = fn(ctx.handle, pa, n, pb, m, ctypes.byref(sch), flags, ctypes.byref(res))
+    _check(ctx, st)
+    out = _result(res)
+    lib().sw_result_free(ctypes.byref(res))
+    return out
+
+
+def sw_score(ctx: Context, a, b, scheme: Scheme | None = None, flags: int = 0) -> Result:
+    """Best local score and end point (Sec. 2, forward pass with pruning)."""
+    return _pairwise(lib().sw_score, ctx, a, b, scheme, flags)
+
+
+def sw_align(ctx: Context, a, b, scheme: Scheme | None = None, flags: int = 0) -> Result:
+    """Score, start/end point and canonical CIGAR (Sec. 2, all three phases)."""
+    return _pairwise(lib().sw_align, ctx, a, b, scheme, flags)
+
+
+def sw_score_plain(ctx: Context, a, b, scheme: Scheme | None = None, flags: int = 0) -> Result:
+    """The plain anti-diagonal GPU baseline (one thread per cell, one launch per diagonal)."""
+    return _pairwise(lib().sw_score_plain, ctx, a, b, scheme, flags)
+
+
+def sw_align_batch(ctx: Context, pairs, scheme: Scheme | None = None, flags: int = 0):
+    """Many pairs in one persistent launch; returns one Result per pair, in order."""
+    cp = (_Pair * max(1, len(pairs)))()
+    keep = []
+    dev = None
+    for k, (a, b) in enumerate(pairs):
+        pa, n, da, ka = _seq(a)
+        pb, m, db, kb = _seq(b)
+        if da != db or (dev is not None and dev != da):
+            raise ValueError("all sequences must be host, or all device")
+        dev = da
+        keep += [ka, kb]
+        cp[k] = _Pair(pa, n, pb, m)
+    if dev:
+        flags |= SW_FLAG_DEVICE_INPUT
+    sch, kk = (scheme or DNA)._c()
+    outs = (_Result * max(1, len(pairs)))()
+    st = lib().sw_align_batch(ctx.handle, cp, len(pairs), ctypes.byref(sch), flags, outs)
+    _check(ctx, st)
+    res = [_result(outs[k]) for k in range(len(pairs))]
+    for k in range(len(pairs)):
+        lib().sw_result_free(ctypes.byref(outs[k]))
+    return res

@@ -1,0 +1,407 @@
+// api.cu -- the C ABI (include/swgb.h): context, validation, forward-pass driver,
+// sw_score and the plain baseline.  sw_align lives in align.cu, the batch path in
+// batch.cu.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "common.cuh"
+#include "ctx.h"
+
+using namespace swgb;
+
+namespace swgb {
+
+int set_cuda_error(sw_ctx *ctx, cudaError_t e, const char *where)
+{
+    if (ctx) {
+        char buf[256];
+        snprintf(buf, sizeof buf, "%s: %s", where, cudaGetErrorString(e));
+        ctx->last_error = buf;
+    }
+    cudaGetLastError();   // clear sticky-free errors
+    return SW_ECUDA;
+}
+
+int build_scheme(const sw_scheme *s, SchemeDev *out)
+{
+    if (!s) return SW_EINVAL;
+    if (s->alphabet < 1 || s->alphabet > 8) return SW_EINVAL;
+    if (s->gap_extend < 1 || s->gap_open < s->gap_extend || s->gap_open > 65535) return SW_EINVAL;
+    SchemeDev d;
+    d.alphabet = s->alphabet;
+    d.go = s->gap_open;
+    d.ge = s->gap_extend;
+    std::memset(d.table, 0, sizeof d.table);
+    int mx = -1000, mn = 1000;
+    for (int x = 0; x < s->alphabet; ++x)
+        for (int y = 0; y < s->alphabet; ++y) {
+            int v;
+            if (s->matrix) v = s->matrix[x * s->alphabet + y];
+            else v = (x == y && x < 4) ? s->match : s->mismatch;
+            if (v < -127 || v > 127) return SW_EINVAL;
+            d.table[x * 8 + y] = (int8_t)v;
+            mx = std::max(mx, v);
+            mn = std::min(mn, v);
+        }
+    if (mx <= 0) return SW_EINVAL;          // a local alignment needs a positive score
+    d.max_sub = mx;
+    d.min_sub = mn;
+    for (int x = 0; x < 8; ++x) {
+        uint32_t lo = 0, hi = 0;
+        for (int y = 0; y < 4; ++y) lo |= (uint32_t)(uint8_t)d.table[x * 8 + y] << (8 * y);
+        for (int y = 0; y < 4; ++y) hi |= (uint32_t)(uint8_t)d.table[x * 8 + 4 + y] << (8 * y);
+        d.prof_lo[x] = lo;
+        d.prof_hi[x] = hi;
+    }
+    *out = d;
+    return SW_OK;
+}
+
+static int occupancy_ctas(sw_ctx *ctx, int rpt, bool p2)
+{
+    int per_sm = 0;
+    if (fwd_occupancy(rpt, p2, 128, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+    if (ctx->opt.warps_per_sm > 0) per_sm = std::max(1, std::min(per_sm, ctx->opt.warps_per_sm / 4));
+    return per_sm * ctx->sms;
+}
+
+int run_forward(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &jobs, bool prune,
+                int rpt, std::vector<int4> &res, sw_stats *stats, float *ms)
+{
+    const int np = (int)jobs.size();
+    res.assign(np, make_int4(0, 0, 0, 0));
+    if (np == 0) return SW_OK;
+    const int R = 32 * rpt;
+    Scope sc_(ctx->arena);
+    std::vector<FwdProblem> hp(np);
+    int64_t ntk = 0;
+    for (int p = 0; p < np; ++p) {
+        const FwdJob &j = jobs[p];
+        FwdProblem &q = hp[p];
+        q.a = j.a; q.b = j.b; q.n = j.n; q.m = j.m;
+        q.nbands = (j.n + R - 1) / R;
+        q.mode = j.mode; q.target = j.target; q.transposed = j.transposed;
+        q.bus = sc_.get<int2>((size_t)j.m);
+        q.flags = sc_.get<int32_t>((size_t)(j.m + CH - 1) / CH);
+        q.band_res = sc_.get<int4>((size_t)q.nbands);
+        ntk += q.nbands;
+    }
+    int32_t *ctrs = sc_.get<int32_t>(4 * (size_t)np + 8);      // best, stop, ovf per problem + globals
+    unsigned long long *dstats = sc_.get<unsigned long long>(4);
+    FwdProblem *dprobs = sc_.get<FwdProblem>(np);
+    int2 *dtk = sc_.get<int2>((size_t)ntk);
+    int4 *dres = sc_.get<int4>(np);
+    if (sc_.failed()) { ctx->last_error = "workspace too small for the forward pass"; return SW_ENOMEM; }
+    for (int p = 0; p < np; ++p) {
+        hp[p].best = ctrs + 8 + 3 * p;
+        hp[p].stop_band = ctrs + 8 + 3 * p + 1;
+        hp[p].ovf = ctrs + 8 + 3 * p + 2;
+    }
+    // ticket order: by band index first (every problem's band b after its band b-1),
+    // larger problems first within a band index
+    std::vector<int> order(np);
+    for (int p = 0; p < np; ++p) order[p] = p;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return (int64_t)hp[x].n * hp[x].m > (int64_t)hp[y].n * hp[y].m;
+    });
+    std::vector<int2> tk;
+    tk.reserve((size_t)ntk);
+    if (np == 1) {
+        for (int b = 0; b < hp[0].nbands; ++b) tk.push_back(make_int2(0, b));
+    } else {
+        // priority = remaining chain (bands left * lag + own width), larger first
+        struct T { int64_t key; int p, b; };
+        std::vector<T> all;
+        all.reserve((size_t)ntk);
+        for (int p = 0; p < np; ++p)
+            for (int b = 0; b < hp[p].nbands; ++b)
+                all.push_back({(int64_t)(hp[p].nbands - b) * 96 + hp[p].m, p, b});
+        std::stable_sort(all.begin(), all.end(), [](const T &x, const T &y) {
+            return x.key > y.key || (x.key == y.key && (x.p < y.p || (x.p == y.p && x.b < y.b)));
+        });
+        for (auto &t : all) tk.push_back(make_int2(t.p, t.b));
+    }
+    cudaStream_t s = ctx->stream;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(dprobs, hp.data(), sizeof(FwdProblem) * np, cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(dtk, tk.data(), sizeof(int2) * tk.size(), cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemsetAsync(ctrs, 0, sizeof(int32_t) * 8, s)) ||
+        (e = cudaMemsetAsync(dstats, 0, sizeof(unsigned long long) * 4, s)))
+        return set_cuda_error(ctx, e, "forward setup");
+    // local: bus row 0 = {0, -go}; anchored: -inf everywhere (biased 0)
+    const bool anch = jobs[0].mode == FWD_ANCHORED;
+    if ((e = fwd_init_launch(dprobs, np, hp.data(), 0, anch ? 0 : -sc.go, s)))
+        return set_cuda_error(ctx, e, "forward init");
+    FwdParams P;
+    std::memset(&P, 0, sizeof P);
+    P.probs = dprobs;
+    P.tickets = dtk;
+    P.ntickets = (int32_t)ntk;
+    P.ticket_ctr = ctrs;
+    P.err = ctrs + 1;
+    P.stats = dstats;
+    for (int x = 0; x < 8; ++x) { P.prof_lo[x] = sc.prof_lo[x]; P.prof_hi[x] = sc.prof_hi[x]; }
+    P.go = sc.go; P.ge = sc.ge; P.max_sub = sc.max_sub;
+    P.prune = prune ? 1 : 0;
+    P.fault_band = ctx->opt.fault_band;
+    P.timeout_ns = (unsigned long long)ctx->opt.timeout_ms * 1000000ull;
+    const bool p2 = sc.alphabet > 4;
+    int ctas = occupancy_ctas(ctx, rpt, p2);
+    ctas = (int)std::min<int64_t>(ctas, (ntk + 3) / 4);
+    cudaEventRecord(ctx->ev[0], s);
+    if ((e = fwd_launch(P, rpt, p2, ctas, 128, s))) return set_cuda_error(ctx, e, "forward launch");
+    cudaEventRecord(ctx->ev[1], s);
+    if ((e = fwd_reduce_launch(dprobs, np, dres, s))) return set_cuda_error(ctx, e, "forward reduce");
+    int32_t herr = 0;
+    unsigned long long hst[4];
+    if ((e = cudaMemcpyAsync(res.data(), dres, sizeof(int4) * np, cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(&herr, ctrs + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(hst, dstats, sizeof hst, cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s)))
+        return set_cuda_error(ctx, e, "forward pass");
+    if (ms) cudaEventElapsedTime(ms, ctx->ev[0], ctx->ev[1]);
+    if (stats) {
+        stats->cells_computed += (int64_t)hst[0];
+        stats->tiles_total += (int64_t)hst[1];
+        stats->tiles_pruned += (int64_t)hst[2];
+    }
+    if (herr == DEV_ETIMEOUT) { ctx->last_error = "device-side inter-band wait timed out"; return SW_ETIMEOUT; }
+    if (herr) { ctx->last_error = "device error word set"; return SW_ECUDA; }
+    return SW_OK;
+}
+
+// copy (or borrow) a sequence to the device and check its codes
+int stage_seq(sw_ctx *ctx, Scope &sc, const uint8_t *p, int64_t len, int alph, bool dev_in,
+              const uint8_t **out)
+{
+    if (len == 0) { *out = nullptr; return SW_OK; }
+    if (!p) return SW_EINVAL;
+    if (!dev_in) {
+        for (int64_t i = 0; i < len; ++i)
+            if (p[i] >= alph) { ctx->last_error = "sequence code >= alphabet"; return SW_EINVAL; }
+        uint8_t *d = sc.get<uint8_t>((size_t)len);
+        if (!d) { ctx->last_error = "workspace too small for the sequences"; return SW_ENOMEM; }
+        cudaError_t e = cudaMemcpyAsync(d, p, (size_t)len, cudaMemcpyHostToDevice, ctx->stream);
+        if (e) return set_cuda_error(ctx, e, "sequence copy");
+        *out = d;
+        return SW_OK;
+    }
+    int32_t *bad = sc.get<int32_t>(1);
+    if (!bad) return SW_ENOMEM;
+    int32_t hbad = 0;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(bad, 0, 4, ctx->stream)) ||
+        (e = check_codes_launch(p, len, alph, bad, ctx->stream)) ||
+        (e = cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, ctx->stream)) ||
+        (e = cudaStreamSynchronize(ctx->stream)))
+        return set_cuda_error(ctx, e, "sequence check");
+    if (hbad) { ctx->last_error = "sequence code >= alphabet"; return SW_EINVAL; }
+    *out = p;
+    return SW_OK;
+}
+
+int validate_lengths(sw_ctx *ctx, int64_t n, int64_t m, const SchemeDev &sc)
+{
+    if (n < 0 || m < 0 || n > 0x7fffffff - 1024 || m > 0x7fffffff - 1024) {
+        ctx->last_error = "sequence length out of range";
+        return SW_EINVAL;
+    }
+    const int64_t mn = std::min(n, m);
+    const int64_t worst = (int64_t)sc.max_sub * mn + (int64_t)std::max(-sc.min_sub, sc.go) * (n + m) +
+                          (int64_t)sc.go;
+    if (worst >= (int64_t)1 << 29) {
+        ctx->last_error = "score range exceeds the int32 kernels (max score * length too large)";
+        return SW_EINVAL;
+    }
+    return SW_OK;
+}
+
+}  // namespace swgb
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+const char *sw_strerror(int st)
+{
+    switch (st) {
+    case SW_OK: return "ok";
+    case SW_EINVAL: return "invalid argument";
+    case SW_ENOMEM: return "workspace too small";
+    case SW_ECUDA: return "CUDA error";
+    case SW_ETIMEOUT: return "device-side wait timed out";
+    case SW_EBUSY: return "request refused by admission";
+    case SW_ENOTIMPL: return "not implemented";
+    case SW_EPENDING: return "result pending";
+    default: return "unknown status";
+    }
+}
+
+int sw_ctx_create(int device, void *stream, void *workspace, uint64_t workspace_bytes, sw_ctx **out)
+{
+    if (!out) return SW_EINVAL;
+    *out = nullptr;
+    if (workspace_bytes < (1u << 20)) return SW_EINVAL;
+    cudaError_t e = cudaSetDevice(device);
+    if (e) return set_cuda_error(nullptr, e, "cudaSetDevice");
+    sw_ctx *c = new (std::nothrow) sw_ctx();
+    if (!c) return SW_ENOMEM;
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, device))) { delete c; return set_cuda_error(nullptr, e, "props"); }
+    c->sms = prop.multiProcessorCount;
+    if (workspace) {
+        c->ws = (char *)workspace;
+    } else {
+        if ((e = cudaMalloc((void **)&c->ws, workspace_bytes))) { delete c; return set_cuda_error(nullptr, e, "cudaMalloc"); }
+        c->owns_ws = true;
+    }
+    c->ws_bytes = workspace_bytes;
+    c->arena.reset(c->ws, workspace_bytes);
+    for (auto &ev : c->ev) cudaEventCreate(&ev);
+    *out = c;
+    return SW_OK;
+}
+
+void sw_ctx_destroy(sw_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream); else cudaDeviceSynchronize();
+    for (auto &ev : ctx->ev) if (ev) cudaEventDestroy(ev);
+    if (ctx->owns_ws && ctx->ws) cudaFree(ctx->ws);
+    delete ctx;
+}
+
+const char *sw_ctx_last_error(const sw_ctx *ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+int sw_ctx_set_option(sw_ctx *ctx, int option, int64_t value)
+{
+    if (!ctx) return SW_EINVAL;
+    switch (option) {
+    case SW_OPT_ROWS_PER_THREAD:
+        if (!fwd_rpt_supported((int)value)) return SW_EINVAL;
+        ctx->opt.rows_per_thread = (int)value; return SW_OK;
+    case SW_OPT_WARPS_PER_SM:
+        if (value < 0 || value > 64) return SW_EINVAL;
+        ctx->opt.warps_per_sm = (int)value; return SW_OK;
+    case SW_OPT_TIMEOUT_MS:
+        if (value < 1 || value > 600000) return SW_EINVAL;
+        ctx->opt.timeout_ms = value; return SW_OK;
+    case SW_OPT_FAULT_BAND:
+        if (value < -1 || value > 0x7fffffff) return SW_EINVAL;
+        ctx->opt.fault_band = (int)value; return SW_OK;
+    case SW_OPT_CKPT_BANDS:
+        if (value < 0 || value > 1000000) return SW_EINVAL;
+        ctx->opt.ckpt_bands = (int)value; return SW_OK;
+    case SW_OPT_LEAF_CELLS:
+        if (value < 256 || value > (1 << 18)) return SW_EINVAL;
+        ctx->opt.leaf_cells = value; return SW_OK;
+    default: return SW_EINVAL;
+    }
+}
+
+static void clear_result(sw_result *out)
+{
+    std::memset(out, 0, sizeof *out);
+    out->a_begin = out->a_end = out->b_begin = out->b_end = -1;
+}
+
+int sw_score(sw_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64_t m,
+             const sw_scheme *scheme, int32_t flags, sw_result *out)
+{
+    if (!ctx || !out) return SW_EINVAL;
+    clear_result(out);
+    std::lock_guard<std::mutex> g(ctx->call_mu);
+    SchemeDev sc;
+    int st = build_scheme(scheme, &sc);
+    if (st) { ctx->last_error = "invalid scheme"; return st; }
+    if ((st = validate_lengths(ctx, n, m, sc))) return st;
+    out->stats.cells = n * m;
+    if (n == 0 || m == 0) return SW_OK;
+    cudaSetDevice(ctx->device);
+    Scope s(ctx->arena);
+    const uint8_t *da = nullptr, *db = nullptr;
+    const bool dev = (flags & SW_FLAG_DEVICE_INPUT) != 0;
+    if ((st = stage_seq(ctx, s, a, n, sc.alphabet, dev, &da))) return st;
+    if ((st = stage_seq(ctx, s, b, m, sc.alphabet, dev, &db))) return st;
+    std::vector<FwdJob> jobs(1);
+    jobs[0] = {da, db, (int32_t)n, (int32_t)m, FWD_LOCAL, 0, 0};
+    std::vector<int4> res;
+    float ms = 0;
+    st = run_forward(ctx, sc, jobs, !(flags & SW_FLAG_NO_PRUNE), ctx->opt.rows_per_thread, res,
+                     &out->stats, &ms);
+    out->stats.ms_forward = ms;
+    if (st) return st;
+    if (res[0].w && res[0].x > 0) {
+        out->score = res[0].x;
+        out->a_end = res[0].y;
+        out->b_end = res[0].z;
+    }
+    return SW_OK;
+}
+
+int sw_score_plain(sw_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64_t m,
+                   const sw_scheme *scheme, int32_t flags, sw_result *out)
+{
+    if (!ctx || !out) return SW_EINVAL;
+    clear_result(out);
+    std::lock_guard<std::mutex> g(ctx->call_mu);
+    SchemeDev sc;
+    int st = build_scheme(scheme, &sc);
+    if (st) return st;
+    if ((st = validate_lengths(ctx, n, m, sc))) return st;
+    if (n >= (1 << 20) - 1 || m >= (1 << 20) - 1) { ctx->last_error = "plain path limited to 2^20"; return SW_EINVAL; }
+    out->stats.cells = n * m;
+    if (n == 0 || m == 0) return SW_OK;
+    cudaSetDevice(ctx->device);
+    Scope s(ctx->arena);
+    const uint8_t *da = nullptr, *db = nullptr;
+    const bool dev = (flags & SW_FLAG_DEVICE_INPUT) != 0;
+    if ((st = stage_seq(ctx, s, a, n, sc.alphabet, dev, &da))) return st;
+    if ((st = stage_seq(ctx, s, b, m, sc.alphabet, dev, &db))) return st;
+    int32_t *tab = s.get<int32_t>(64);
+    int32_t *bufs = s.get<int32_t>(9 * (size_t)(n + 2));
+    unsigned long long *key = s.get<unsigned long long>(1);
+    if (s.failed()) return SW_ENOMEM;
+    int32_t htab[64];
+    for (int x = 0; x < sc.alphabet; ++x)
+        for (int y = 0; y < sc.alphabet; ++y) htab[x * sc.alphabet + y] = sc.table[x * 8 + y];
+    cudaError_t e;
+    cudaStream_t strm = ctx->stream;
+    if ((e = cudaMemcpyAsync(tab, htab, sizeof htab, cudaMemcpyHostToDevice, strm)) ||
+        (e = cudaMemsetAsync(key, 0, 8, strm)) ||
+        (e = cudaMemsetAsync(bufs, 0, sizeof(int32_t) * 9 * (size_t)(n + 2), strm)))
+        return set_cuda_error(ctx, e, "plain setup");
+    cudaEventRecord(ctx->ev[0], strm);
+    if ((e = plain_score(da, (int)n, db, (int)m, tab, sc.alphabet, sc.go, sc.ge, bufs, key, strm)))
+        return set_cuda_error(ctx, e, "plain launch");
+    cudaEventRecord(ctx->ev[1], strm);
+    unsigned long long hk = 0;
+    if ((e = cudaMemcpyAsync(&hk, key, 8, cudaMemcpyDeviceToHost, strm)) || (e = cudaStreamSynchronize(strm)))
+        return set_cuda_error(ctx, e, "plain pass");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+    out->stats.ms_forward = ms;
+    out->stats.cells_computed = n * m;
+    if (hk) {
+        out->score = (int64_t)(hk >> 40);
+        out->a_end = (1 << 20) - 1 - (int64_t)((hk >> 20) & 0xFFFFF);
+        out->b_end = (1 << 20) - 1 - (int64_t)(hk & 0xFFFFF);
+    }
+    return SW_OK;
+}
+
+void sw_result_free(sw_result *r)
+{
+    if (!r) return;
+    free(r->cigar);
+    r->cigar = nullptr;
+    r->cigar_len = 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// common.cuh -- device helpers shared by the sm_103a kernels of the library.
+//
+// Integer max-plus helpers (DPX: VIMNMX / VIADDMNMX on Hopper and later),
+// the byte permute used to look up substitution scores, acquire/release
+// accessors for the inter-band progress flags, and the bounded wait that
+// every inter-warp dependency goes through.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace swgb {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int CH = 32;                 // columns per boundary chunk (one per lane)
+constexpr int BIAS = 1 << 30;          // global-mode offset: biased 0 is -infinity
+constexpr uint32_t VIRTUAL_PROF = 0x80808080u;  // -128 for rows past the end
+
+// error codes written to the device error word (mirror sw_status)
+constexpr int DEV_ETIMEOUT = 4;
+
+// ---------------------------------------------------------------- arithmetic
+// max(a + b, c)
+__device__ __forceinline__ int addmax(int a, int b, int c) { return __viaddmax_s32(a, b, c); }
+// max(a + b, c, 0)
+__device__ __forceinline__ int addmax0(int a, int b, int c) { return __viaddmax_s32_relu(a, b, c); }
+__device__ __forceinline__ int imax(int a, int b) { return max(a, b); }
+__device__ __forceinline__ int imax3(int a, int b, int c) { return __vimax3_s32(a, b, c); }
+
+// Substitution score lookup: the profile word holds s(a_row, c) for b codes
+// c = 0..3 as four signed bytes (a second word holds c = 4..7).  `sel` is the
+// prmt selector of the column code: byte c, then three sign-replicating copies,
+// so the result is the selected byte sign-extended to 32 bits.
+__device__ __forceinline__ int sub_lookup(uint32_t lo, uint32_t hi, uint32_t sel) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(lo), "r"(hi), "r"(sel));
+    return (int)r;
+}
+__host__ __device__ __forceinline__ uint32_t code_selector(uint32_t c) {
+    uint32_t s = c | 8u;
+    return c | (s << 4) | (s << 8) | (s << 12);
+}
+
+// ---------------------------------------------------------------- memory
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile(const int *p) {
+    return *(const volatile int *)p;
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait until *flag >= need.  Called by one lane.  Returns 1 when the
+// flag is reached, 0 when the call must abandon the band: the error word is
+// set (by anyone), `*cancel` exceeds `cancel_above`, or the wait ran past
+// `limit_ns`, in which case this wait records DEV_ETIMEOUT in the error word.
+__device__ __forceinline__ int wait_flag(const int *flag, int need, int *err,
+                                         const int *cancel, int cancel_above,
+                                         unsigned long long limit_ns) {
+    if (ld_acquire(flag) >= need) return 1;
+    unsigned long long t0 = globaltimer();
+    unsigned ns = 64;
+    for (;;) {
+        if (ld_acquire(flag) >= need) return 1;
+        if (ld_volatile(err)) return 0;
+        if (cancel && ld_volatile(cancel) < cancel_above) return 0;
+        if (globaltimer() - t0 > limit_ns) {
+            atomicCAS(err, 0, DEV_ETIMEOUT);
+            return 0;
+        }
+        __nanosleep(ns);
+        if (ns < 2048) ns <<= 1;
+    }
+}
+
+}  // namespace swgb

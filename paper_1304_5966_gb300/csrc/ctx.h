@@ -1,0 +1,146 @@
+// ctx.h -- host-side context, workspace arena and shared driver helpers.
+#pragma once
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/swgb.h"
+#include "kernels.h"
+
+namespace swgb {
+
+// First-fit sub-allocator over the context's device workspace (256-byte aligned).
+class Arena {
+public:
+    void reset(char *base, size_t bytes) {
+        base_ = base; bytes_ = bytes; free_.clear(); used_.clear();
+        if (bytes) free_[0] = bytes;
+    }
+    void *alloc(size_t bytes) {
+        bytes = (bytes + 255) & ~size_t(255);
+        if (bytes == 0) bytes = 256;
+        std::lock_guard<std::mutex> g(mu_);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                size_t off = it->first, rest = it->second - bytes;
+                free_.erase(it);
+                if (rest) free_[off + bytes] = rest;
+                used_[off] = bytes;
+                return base_ + off;
+            }
+        }
+        return nullptr;
+    }
+    void release(void *p) {
+        if (!p) return;
+        std::lock_guard<std::mutex> g(mu_);
+        size_t off = (size_t)((char *)p - base_);
+        auto u = used_.find(off);
+        if (u == used_.end()) return;
+        size_t sz = u->second;
+        used_.erase(u);
+        auto nx = free_.lower_bound(off);
+        if (nx != free_.end() && nx->first == off + sz) { sz += nx->second; nx = free_.erase(nx); }
+        if (nx != free_.begin()) {
+            auto pv = std::prev(nx);
+            if (pv->first + pv->second == off) { pv->second += sz; return; }
+        }
+        free_[off] = sz;
+    }
+    size_t largest_free() const {
+        std::lock_guard<std::mutex> g(mu_);
+        size_t best = 0;
+        for (auto &f : free_) best = f.second > best ? f.second : best;
+        return best;
+    }
+    size_t free_bytes() const {
+        std::lock_guard<std::mutex> g(mu_);
+        size_t t = 0;
+        for (auto &f : free_) t += f.second;
+        return t;
+    }
+    size_t capacity() const { return bytes_; }
+private:
+    char *base_ = nullptr;
+    size_t bytes_ = 0;
+    std::map<size_t, size_t> free_;
+    std::map<size_t, size_t> used_;
+    mutable std::mutex mu_;
+};
+
+// Allocations of one call, released together (RAII).
+class Scope {
+public:
+    explicit Scope(Arena &a) : a_(a) {}
+    ~Scope() { for (void *p : ptrs_) a_.release(p); }
+    template <class T> T *get(size_t count) {
+        void *p = a_.alloc(sizeof(T) * (count ? count : 1));
+        if (!p) { failed_ = true; return nullptr; }
+        ptrs_.push_back(p);
+        return (T *)p;
+    }
+    bool failed() const { return failed_; }
+private:
+    Arena &a_;
+    std::vector<void *> ptrs_;
+    bool failed_ = false;
+};
+
+// Scheme as the kernels consume it.
+struct SchemeDev {
+    int alphabet = 4;
+    int go = 5, ge = 2;
+    int max_sub = 1;
+    int min_sub = -3;
+    int8_t table[64];          // 8 x 8 row-major (a code, b code)
+    uint32_t prof_lo[8], prof_hi[8];
+};
+
+struct Options {
+    int rows_per_thread = 16;
+    int warps_per_sm = 0;          // 0 = occupancy limit
+    int64_t timeout_ms = 2000;
+    int fault_band = -1;
+    int ckpt_bands = 0;            // 0 = choose from the workspace size
+    int64_t leaf_cells = 1 << 16;
+};
+
+}  // namespace swgb
+
+struct sw_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool owns_ws = false;
+    int sms = 0;
+    swgb::Arena arena;
+    swgb::Options opt;
+    std::string last_error;
+    cudaEvent_t ev[8] = {};
+    std::mutex call_mu;
+};
+
+namespace swgb {
+
+int set_cuda_error(sw_ctx *ctx, cudaError_t e, const char *where);
+int build_scheme(const sw_scheme *s, SchemeDev *out);
+
+// Forward pass over a set of problems (one persistent launch).  res[p] receives
+// {score, row, col, found} (biased in anchored mode).  stats may be null.
+struct FwdJob {
+    const uint8_t *a;      // device
+    const uint8_t *b;      // device
+    int32_t n, m;
+    int32_t mode;          // FwdMode
+    int32_t target;        // anchored: biased target
+    int32_t transposed;
+};
+int run_forward(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &jobs, bool prune,
+                int rpt, std::vector<int4> &res, sw_stats *stats, float *ms);
+
+}  // namespace swgb
