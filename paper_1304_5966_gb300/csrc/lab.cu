@@ -1,0 +1,362 @@
+// lab.cu -- the reconstruction pass: global affine alignment between two path
+// nodes with crossing labels (sm_103a).
+//
+// The paper reconstructs the alignment between start and end point with a
+// modified Myers-Miller divide and conquer whose parts are solved by the same
+// wavefront method (Sec. 2, reconstruction paragraph).  A Myers-Miller midpoint
+// has no tie rule, so this pass splits the problem differently: every node
+// (cell x state) takes, during the forward sweep, the predecessor the greedy
+// traceback would take (diagonal > vertical > horizontal; open > extend) and
+// inherits that predecessor's label.  Rows at the bottom of every ck-th band are
+// checkpoints: the next band starts fresh labels that name the edge crossing
+// from the checkpoint row, and the checkpoint row's values and labels are saved.
+// The sink's label names the last crossing; the saved label of that crossing's
+// source names the one before, and so on (walk kernel below).  The path segment
+// between two consecutive crossings is itself the greedy traceback of that
+// strip (both end nodes lie on the path), so strips recurse independently.
+//
+// Values are biased by BIAS (biased 0 = minus infinity), no zero floor.  The
+// band pipeline, ticket queue, bounded waits and pruning follow fwd.cu; the
+// pruning bound here also charges ge per unavoidable gap column, since the sink
+// is fixed, and compares with the known optimum at the sink.
+#include "common.cuh"
+#include "lab.h"
+
+namespace swgb {
+
+__device__ __forceinline__ int border_cost(int k, bool cont, int go, int ge)
+{
+    // cost of k >= 1 gap columns leaving the source: a continued gap pays ge each
+    return cont ? ge * k : go + ge * (k - 1);
+}
+
+template <int RPT, bool PREF_VERT, bool PROF2>
+__global__ void __launch_bounds__(128) lab_kernel(const LabParams P)
+{
+    __shared__ int4 s_in_all[4][2][CH];      // {H, F, labH, labF} of the row above
+    __shared__ int4 s_out_all[4][2 * CH];    // bottom row ring
+    __shared__ uint32_t s_sel_all[4][2][CH]; // column selectors
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    int4 (*s_in)[CH] = s_in_all[wid];
+    int4 *s_out = s_out_all[wid];
+    uint32_t (*s_sel)[CH] = s_sel_all[wid];
+    const int go = P.go, ge = P.ge;
+    constexpr int R = 32 * RPT;
+
+    for (;;) {
+        int tk = 0, stop_now = 0;
+        if (lane == 0) { tk = atomicAdd(P.ticket_ctr, 1); stop_now = ld_volatile(P.err); }
+        tk = __shfl_sync(FULL, tk, 0);
+        stop_now = __shfl_sync(FULL, stop_now, 0);
+        if (tk >= P.ntickets || stop_now) return;
+        const int2 tb = P.tickets[tk];
+        const LabProblem &pr = P.probs[tb.x];
+        const int band = tb.y;
+        const int n = pr.n, m = pr.m, ck = pr.ck;
+        const uint8_t *__restrict__ bseq = pr.b;
+        int4 *__restrict__ bus = pr.bus;
+        int *__restrict__ flags = pr.flags;
+        const int need = band - 1;
+        const bool fresh = ck > 0 && band > 0 && (band % ck) == 0;
+        const bool ckpt_band = ck > 0 && ((band + 1) % ck) == 0 && band + 1 < pr.nbands;
+        int4 *ck_row = ckpt_band ? pr.ckpt + (size_t)((band + 1) / ck - 1) * (size_t)m : nullptr;
+        const bool src_f = pr.src == ST_F, src_e = pr.src == ST_E;
+        const int blab = (ck > 0 && band >= ck) ? ((0 << 2) | (go == ge ? LAB_OPEN : LAB_EXT)) : LAB_INIT;
+        const int prev_blab = (ck > 0 && band - 1 >= ck) ? ((0 << 2) | (go == ge ? LAB_OPEN : LAB_EXT)) : LAB_INIT;
+
+        const int rowbase = band * R + lane * RPT;   // 0-based row index of the lane's first row
+        uint32_t plo[RPT], phi[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int r = rowbase + k;
+            uint32_t lo = VIRTUAL_PROF, hi = VIRTUAL_PROF;
+            if (r < n) {
+                const int c = pr.a[r] & 7;
+                lo = P.prof_lo[c];
+                if (PROF2) hi = P.prof_hi[c];
+            }
+            plo[k] = lo;
+            phi[k] = PROF2 ? hi : 0u;
+        }
+        // column 0 border: H(i,0) = F(i,0) = BIAS - cost(i); E(i,0) = -inf
+        int Hl[RPT], E[RPT], lHl[RPT], lE[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int i = rowbase + k + 1;
+            Hl[k] = max(0, BIAS - border_cost(i, src_f, go, ge));
+            E[k] = 0;
+            lHl[k] = blab;
+            lE[k] = LAB_INIT;
+        }
+        int Hlast = Hl[RPT - 1], Flast = 0, lHlast = blab, lFlast = LAB_INIT;
+        uint32_t sellast = 0;
+        int updiag, lupdiag;
+        if (band == 0) { updiag = (lane == 0) ? BIAS : Hl[0]; lupdiag = LAB_INIT; }
+        else { updiag = max(0, BIAS - border_cost(rowbase, src_f, go, ge)); lupdiag = lane ? blab : prev_blab; }
+        if (lane > 0) {
+            // H(row above the lane, 0): the previous lane's last row
+            updiag = max(0, BIAS - border_cost(rowbase, src_f, go, ge));
+            lupdiag = blab;
+        }
+        // sink bookkeeping
+        const int sink_k = n - 1 - rowbase;            // row n lives at k = sink_k in this lane
+        const bool has_sink = sink_k >= 0 && sink_k < RPT;
+        bool aborted = false;
+        unsigned tiles = 0, pruned = 0;
+
+        const int nch = (m + CH - 1) / CH;
+        const int nblk = nch + 1;
+        const int rows_left = n - band * R;
+        {
+            int ok = 1;
+            if (lane == 0) ok = wait_flag(&flags[0], need, P.err, nullptr, 0, P.timeout_ns);
+            ok = __shfl_sync(FULL, ok, 0);
+            if (!ok) aborted = true;
+            else {
+                int4 v = make_int4(0, 0, LAB_INIT, LAB_INIT);
+                uint32_t sel = 0;
+                if (lane < m) { v = bus[lane]; sel = code_selector(bseq[lane]); }
+                s_in[0][lane] = v;
+                s_sel[0][lane] = sel;
+            }
+            __syncwarp();
+        }
+        for (int q = 0; q < nblk && !aborted; ++q) {
+            const int buf = q & 1;
+            const bool has_next = (q + 1) < nch;
+            int ready = 0;
+            int4 nv = make_int4(0, 0, LAB_INIT, LAB_INIT);
+            uint32_t nsel = 0;
+            const int ncol = (q + 1) * CH + lane;
+            if (has_next) {
+                if (lane == 0) ready = ld_acquire(&flags[q + 1]) >= need;
+                ready = __shfl_sync(FULL, ready, 0);
+                if (ready && ncol < m) { nv = bus[ncol]; nsel = code_selector(bseq[ncol]); }
+            }
+            bool skip = false;
+            if (P.prune && pr.target > 0) {
+                int mx = 0;
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) mx = max(mx, Hl[k]);
+                mx = max(mx, max(Hlast, updiag));
+                if (q < nch) mx = max(mx, s_in[buf][lane].x);
+                mx = __reduce_max_sync(FULL, mx);
+                // rows / columns still to go from any node this block touches
+                const long long dr_hi = (long long)n - band * R, dr_lo = max(0LL, dr_hi - R);
+                const long long jlo = max(0, q * CH - CH), jhi = min(m, q * CH + CH);
+                const long long dc_hi = m - jlo, dc_lo = m - jhi;
+                long long gapmin = 0;
+                if (dr_lo > dc_hi) gapmin = dr_lo - dc_hi;
+                if (dc_lo > dr_hi) gapmin = dc_lo - dr_hi;
+                const long long gain = (long long)P.max_sub * min(dr_hi, dc_hi) - (long long)ge * gapmin;
+                skip = (long long)mx + gain < (long long)pr.target;
+            }
+            ++tiles;
+            if (skip) {
+                ++pruned;
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) { Hl[k] = 0; E[k] = 0; }
+                Hlast = 0; Flast = 0;
+                if (q < nch) {
+                    sellast = s_sel[buf][31 - lane];
+                    updiag = (lane == 0) ? s_in[buf][31].x : 0;
+                    lupdiag = (lane == 0) ? s_in[buf][31].z : 0;
+                } else { updiag = 0; }
+                const int oc = q * CH - 31 + lane;
+                if (oc >= 0 && oc < m) s_out[oc & 63] = make_int4(0, 0, LAB_INIT, LAB_INIT);
+            } else {
+#pragma unroll 1
+                for (int u = 0; u < CH; ++u) {
+                    const int4 in = s_in[buf][u];
+                    const uint32_t insel = s_sel[buf][u];
+                    const int rH = __shfl_up_sync(FULL, Hlast, 1);
+                    const int rF = __shfl_up_sync(FULL, Flast, 1);
+                    const int rlH = __shfl_up_sync(FULL, lHlast, 1);
+                    const int rlF = __shfl_up_sync(FULL, lFlast, 1);
+                    const uint32_t rS = __shfl_up_sync(FULL, sellast, 1);
+                    const int j = q * CH + u - lane;       // 0-based column; DP column j + 1
+                    int upH, upF, lupH, lupF, ldiag;
+                    const uint32_t sel = lane ? rS : insel;
+                    int diag = updiag;
+                    if (lane) {
+                        upH = rH; upF = rF; lupH = rlH; lupF = rlF; ldiag = lupdiag;
+                    } else {
+                        upH = in.x; upF = in.y;
+                        if (fresh) {
+                            ldiag = (j << 2) | LAB_DIAG;
+                            lupH = ((j + 1) << 2) | LAB_OPEN;
+                            lupF = ((j + 1) << 2) | LAB_EXT;
+                        } else {
+                            ldiag = lupdiag; lupH = in.z; lupF = in.w;
+                        }
+                    }
+                    updiag = upH;
+                    lupdiag = lupH;
+                    sellast = sel;
+                    if ((unsigned)j < (unsigned)m) {
+                        int hgo = upH - go;
+                        int F = upF, lF = lupF, lH = lupH;
+                        const bool sink_step = has_sink && j == m - 1;
+                        int sH = 0, sF = 0, sE = 0, slH = 0, slF = 0, slE = 0;
+#pragma unroll
+                        for (int k = 0; k < RPT; ++k) {
+                            const int s = sub_lookup(plo[k], phi[k], sel);
+                            bool pv, pt, pd, pe;
+                            // F(i,j): open from H(i-1,j) preferred on ties
+                            F = __vibmax_s32(hgo, F - ge, &pv);
+                            lF = pv ? lH : lF;
+                            const int Ein = E[k], lEin = lE[k];
+                            int t, lt;
+                            if (PREF_VERT) { t = __vibmax_s32(F, Ein, &pt); lt = pt ? lF : lEin; }
+                            else { t = __vibmax_s32(Ein, F, &pt); lt = pt ? lEin : lF; }
+                            const int h = __vibmax_s32(diag + s, t, &pd);
+                            const int lh = pd ? ldiag : lt;
+                            diag = Hl[k];
+                            ldiag = lHl[k];
+                            Hl[k] = h;
+                            lHl[k] = lh;
+                            hgo = h - go;
+                            E[k] = __vibmax_s32(hgo, Ein - ge, &pe);   // E(i, j+1)
+                            lE[k] = pe ? lh : lEin;
+                            lH = lh;
+                            if (sink_step && k == sink_k) {
+                                sH = h; sF = F; sE = Ein; slH = lh; slF = lF; slE = lEin;
+                            }
+                        }
+                        Hlast = Hl[RPT - 1]; lHlast = lH;
+                        Flast = F; lFlast = lF;
+                        if (sink_step) {
+                            pr.sink[0] = make_int4(sH, sF, sE, 1);
+                            pr.sink[1] = make_int4(slH, slF, slE, 1);
+                        }
+                        if (lane == 31) s_out[j & 63] = make_int4(Hlast, Flast, lHlast, lFlast);
+                    }
+                }
+            }
+            if (has_next) {
+                if (!ready) {
+                    int ok = 1;
+                    if (lane == 0) ok = wait_flag(&flags[q + 1], need, P.err, nullptr, 0, P.timeout_ns);
+                    ok = __shfl_sync(FULL, ok, 0);
+                    if (!ok) { aborted = true; break; }
+                    if (ncol < m) { nv = bus[ncol]; nsel = code_selector(bseq[ncol]); }
+                }
+                s_in[buf ^ 1][lane] = nv;
+                s_sel[buf ^ 1][lane] = nsel;
+            }
+            __syncwarp();
+            if (q >= 1) {
+                const int col = (q - 1) * CH + lane;
+                if (col < m) {
+                    const int4 o = s_out[col & 63];
+                    bus[col] = o;
+                    if (ck_row) ck_row[col] = o;
+                }
+                __syncwarp();
+                if (lane == 0) st_release(&flags[q - 1], band);
+            }
+        }
+        if (!aborted && lane == 0) {
+            atomicAdd(&P.stats[1], (unsigned long long)tiles);
+            atomicAdd(&P.stats[2], (unsigned long long)pruned);
+            atomicAdd(&P.stats[0], (unsigned long long)(tiles - pruned) * CH *
+                                       (unsigned long long)min(R, rows_left));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void lab_init_kernel(LabProblem *probs, int nprobs, int go, int ge)
+{
+    const int p = blockIdx.x;
+    if (p >= nprobs) return;
+    const LabProblem pr = probs[p];
+    const bool src_e = pr.src == ST_E;
+    for (int j = threadIdx.x; j < pr.m; j += blockDim.x) {
+        // row 0: H(0, j+1) = E(0, j+1) = BIAS - cost(j+1); F = -inf
+        const int c = src_e ? ge * (j + 1) : go + ge * j;
+        pr.bus[j] = make_int4(max(0, BIAS - c), 0, LAB_INIT, LAB_INIT);
+    }
+    const int nch = (pr.m + CH - 1) / CH;
+    for (int c = threadIdx.x; c < nch; c += blockDim.x) pr.flags[c] = -1;
+    if (threadIdx.x == 0) {
+        pr.sink[0] = make_int4(0, 0, 0, 0);
+        pr.sink[1] = make_int4(0, 0, 0, 0);
+    }
+}
+
+// one thread per problem: follow the labels from the sink back through the
+// checkpoint rows.  out[p*stride + t-1] = {col, type, value of the crossing's
+// source node, 0} for checkpoint t = 1..nck; res[p] = {sink value, ok, 0, 0}.
+__global__ void lab_walk_kernel(const LabProblem *probs, int nprobs, int R, int go, int ge,
+                                int4 *out, int stride, int4 *res)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nprobs) return;
+    const LabProblem pr = probs[p];
+    const int4 sv = pr.sink[0], sl = pr.sink[1];
+    int v = pr.snk == ST_H ? sv.x : (pr.snk == ST_F ? sv.y : sv.z);
+    int L = pr.snk == ST_H ? sl.x : (pr.snk == ST_F ? sl.y : sl.z);
+    int ok = sv.w == 1;
+    const int nck = pr.ck > 0 ? (pr.nbands - 1) / pr.ck : 0;
+    const bool src_f = pr.src == ST_F;
+    for (int t = nck; t >= 1 && ok; --t) {
+        const int type = L & 3, c = L >> 2;
+        if (type == LAB_INIT || c < 0 || c > pr.m) { ok = 0; break; }
+        const int st = (type == LAB_EXT) ? ST_F : ST_H;
+        const int r = t * pr.ck * R;         // DP row of checkpoint t
+        int vu, Lp;
+        if (c == 0) {
+            vu = max(0, BIAS - border_cost(r, src_f, go, ge));
+            Lp = (t >= 2) ? ((0 << 2) | (go == ge ? LAB_OPEN : LAB_EXT)) : LAB_INIT;
+        } else {
+            const int4 e = pr.ckpt[(size_t)(t - 1) * pr.m + (c - 1)];
+            vu = st == ST_H ? e.x : e.y;
+            Lp = st == ST_H ? e.z : e.w;
+        }
+        out[(size_t)p * stride + (t - 1)] = make_int4(c, type, vu, r);
+        L = Lp;
+    }
+    res[p] = make_int4(v, ok, nck, 0);
+}
+
+// ---------------------------------------------------------------------------
+template <int RPT, bool PV, bool P2>
+static cudaError_t lab_one(const LabParams &p, int ctas, cudaStream_t s)
+{
+    lab_kernel<RPT, PV, P2><<<ctas, 128, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t lab_launch(const LabParams &p, bool pref_vert, bool p2, int ctas, cudaStream_t s)
+{
+    if (pref_vert) return p2 ? lab_one<LAB_RPT, true, true>(p, ctas, s) : lab_one<LAB_RPT, true, false>(p, ctas, s);
+    return p2 ? lab_one<LAB_RPT, false, true>(p, ctas, s) : lab_one<LAB_RPT, false, false>(p, ctas, s);
+}
+
+cudaError_t lab_occupancy(bool pref_vert, bool p2, int *n)
+{
+    if (pref_vert)
+        return p2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lab_kernel<LAB_RPT, true, true>, 128, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lab_kernel<LAB_RPT, true, false>, 128, 0);
+    return p2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lab_kernel<LAB_RPT, false, true>, 128, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lab_kernel<LAB_RPT, false, false>, 128, 0);
+}
+
+cudaError_t lab_init_launch(LabProblem *probs, int nprobs, int go, int ge, cudaStream_t s)
+{
+    if (nprobs <= 0) return cudaSuccess;
+    lab_init_kernel<<<nprobs, 256, 0, s>>>(probs, nprobs, go, ge);
+    return cudaGetLastError();
+}
+
+cudaError_t lab_walk_launch(const LabProblem *probs, int nprobs, int go, int ge, int4 *out, int stride,
+                            int4 *res, cudaStream_t s)
+{
+    if (nprobs <= 0) return cudaSuccess;
+    lab_walk_kernel<<<(nprobs + 127) / 128, 128, 0, s>>>(probs, nprobs, 32 * LAB_RPT, go, ge, out, stride, res);
+    return cudaGetLastError();
+}
+
+}  // namespace swgb
