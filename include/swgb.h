@@ -89,6 +89,8 @@ typedef struct {
     int32_t int16_reruns;      /* batch: pairs re-run in int32 after int16 overflow */
     int32_t levels;            /* reconstruction: divide-and-conquer levels */
     float ms_forward, ms_start, ms_align;   /* device time per phase */
+    int64_t fwd_cells;         /* cells computed by the forward-pass kernel alone */
+    int64_t kernel_launches;   /* kernels this call launched */
 } sw_stats;
 
 typedef struct {
@@ -118,7 +120,7 @@ const char *sw_ctx_last_error(const sw_ctx *ctx);
 const char *sw_strerror(int status);
 
 /* Tuning / testing knobs (values persist on the context):
- *   SW_OPT_ROWS_PER_THREAD  forward pass rows per thread: 8, 16, 24 or 32
+ *   SW_OPT_ROWS_PER_THREAD  forward pass rows per thread: 8, 16, 24 or 32 (0 = by size)
  *   SW_OPT_WARPS_PER_SM     resident warps per SM for the persistent kernels
  *   SW_OPT_TIMEOUT_MS       limit of every device-side inter-band wait
  *   SW_OPT_FAULT_BAND       testing: this forward-pass band never publishes its
@@ -166,11 +168,14 @@ int sw_score_plain(sw_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, i
 
 void sw_result_free(sw_result *r);
 
-/* Diagnostics: measured issue rate of one instruction kind on `device`, in
- * 32-bit lane operations per SM clock (independent chains, full occupancy):
- * kind 0 IADD, 1 IMNMX, 2 DPX viaddmax, 3 DPX viaddmax relu, 4 PRMT,
- * 5 DPX viaddmax 16x2, 6 the forward pass's per-cell mix (8 ops per cell).
- * Used for the forward pass's issue-rate roofline; allocates its own buffers. */
+/* Diagnostics: measured issue rate on `device`, per SM clock, with independent
+ * chains at full occupancy.  Kinds 0-5, 7, 8, 10 give lane operations per clock
+ * per SM of one instruction: 0 IADD+LOP pair, 1 IMNMX+IADD pair, 2 DPX
+ * viaddmax, 3 viaddmax relu, 4 PRMT, 5 viaddmax 16x2, 7 vimax3, 8 vimax3 relu,
+ * 10 vimax relu + IADD pair.  Kinds 6, 9, 11 give cells per clock per SM of a
+ * whole cell update: 6 the forward pass's form, 9 a vimax3-relu form, 11 the
+ * 16x2 form (two cells per lane).  Used for the forward pass's issue-rate
+ * roofline; allocates its own buffers. */
 int sw_probe_issue_rate(int device, int kind, double *ops_per_clk_per_sm);
 
 #ifdef __cplusplus

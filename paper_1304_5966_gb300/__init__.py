@@ -51,7 +51,8 @@ class _Stats(ctypes.Structure):
                 ("tiles_total", ctypes.c_int64), ("tiles_pruned", ctypes.c_int64),
                 ("int16_reruns", ctypes.c_int32), ("levels", ctypes.c_int32),
                 ("ms_forward", ctypes.c_float), ("ms_start", ctypes.c_float),
-                ("ms_align", ctypes.c_float)]
+                ("ms_align", ctypes.c_float), ("fwd_cells", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64)]
 
 
 class _Result(ctypes.Structure):

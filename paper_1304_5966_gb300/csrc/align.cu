@@ -152,6 +152,7 @@ static int run_label_level(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, 
     if ((e = lab_launch(P, !any_t, p2, ctas, st))) return set_cuda_error(ctx, e, "label launch");
     if ((e = lab_walk_launch(dprobs, np, sc.go, sc.ge, dcross, maxnck, dres, st)))
         return set_cuda_error(ctx, e, "label walk");
+    ctx->launches += 3;
     std::vector<int4> hc((size_t)np * maxnck), hr(np);
     int32_t herr = 0;
     unsigned long long hst[4];
@@ -249,6 +250,7 @@ static int run_leaves(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const
         (e = cudaMemcpyAsync(dtab, sc.table, 64, cudaMemcpyHostToDevice, st)) ||
         (e = leaf_launch(dp, np, dtab, sc.go, sc.ge, max_cells, dops, dlen, st)))
         return set_cuda_error(ctx, e, "leaf launch");
+    ctx->launches += 1;
     std::vector<char> hops((size_t)off);
     std::vector<int32_t> hlen(np);
     if ((e = cudaMemcpyAsync(hops.data(), dops, (size_t)off, cudaMemcpyDeviceToHost, st)) ||
@@ -392,6 +394,7 @@ int find_start(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const uint8_
     cudaError_t e;
     if ((e = reverse_copy_launch(dA, rA, a_end, ctx->stream)) || (e = reverse_copy_launch(dB, rB, b_end, ctx->stream)))
         return set_cuda_error(ctx, e, "reverse copy");
+    ctx->launches += 2;
     std::vector<FwdJob> jobs(1);
     jobs[0] = {rA, rB, (int32_t)a_end, (int32_t)b_end, FWD_ANCHORED, (int32_t)(BIAS + S), 0};
     std::vector<int4> res;
@@ -477,5 +480,8 @@ extern "C" int sw_align(sw_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t 
             return set_cuda_error(ctx, e, "sequence readback");
         pa = ha.data(); pb = hb.data();
     }
-    return align_one(ctx, sc, da, db, pa, pb, n, m, !(flags & SW_FLAG_NO_PRUNE), false, 0, 0, 0, out);
+    const int64_t l0 = ctx->launches;
+    st = align_one(ctx, sc, da, db, pa, pb, n, m, !(flags & SW_FLAG_NO_PRUNE), false, 0, 0, 0, out);
+    out->stats.kernel_launches = ctx->launches - l0;
+    return st;
 }

@@ -67,12 +67,31 @@ static int occupancy_ctas(sw_ctx *ctx, int rpt, bool p2)
     return per_sm * ctx->sms;
 }
 
+// rows per thread when the context leaves it to the library (option 0): the
+// largest band height that still leaves a few bands per resident warp, so the
+// band pipeline stays full; smaller problems get thinner bands.
+static int auto_rpt(sw_ctx *ctx, const std::vector<FwdJob> &jobs, bool p2)
+{
+    int64_t rows = 0;
+    for (auto &j : jobs) rows += j.n;
+    const int cands[4] = {32, 24, 16, 8};
+    const double need[4] = {2.5, 2.5, 1.0, 0.0};
+    for (int k = 0; k < 4; ++k) {
+        int per_sm = 1;
+        if (fwd_occupancy(cands[k], p2, 128, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+        const double warps = 4.0 * per_sm * ctx->sms;
+        if ((double)rows / (32.0 * cands[k]) >= need[k] * warps) return cands[k];
+    }
+    return 8;
+}
+
 int run_forward(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &jobs, bool prune,
                 int rpt, std::vector<int4> &res, sw_stats *stats, float *ms)
 {
     const int np = (int)jobs.size();
     res.assign(np, make_int4(0, 0, 0, 0));
     if (np == 0) return SW_OK;
+    if (rpt <= 0) rpt = auto_rpt(ctx, jobs, sc.alphabet > 4);
     const int R = 32 * rpt;
     Scope sc_(ctx->arena);
     std::vector<FwdProblem> hp(np);
@@ -161,8 +180,10 @@ int run_forward(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &job
         (e = cudaMemcpyAsync(hst, dstats, sizeof hst, cudaMemcpyDeviceToHost, s)) ||
         (e = cudaStreamSynchronize(s)))
         return set_cuda_error(ctx, e, "forward pass");
+    ctx->launches += 3;
     if (ms) cudaEventElapsedTime(ms, ctx->ev[0], ctx->ev[1]);
     if (stats) {
+        if (jobs[0].mode == FWD_LOCAL) stats->fwd_cells += (int64_t)hst[0];
         stats->cells_computed += (int64_t)hst[0];
         stats->tiles_total += (int64_t)hst[1];
         stats->tiles_pruned += (int64_t)hst[2];
@@ -193,7 +214,7 @@ int stage_seq(sw_ctx *ctx, Scope &sc, const uint8_t *p, int64_t len, int alph, b
     int32_t hbad = 0;
     cudaError_t e;
     if ((e = cudaMemsetAsync(bad, 0, 4, ctx->stream)) ||
-        (e = check_codes_launch(p, len, alph, bad, ctx->stream)) ||
+        (e = (++ctx->launches, check_codes_launch(p, len, alph, bad, ctx->stream))) ||
         (e = cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, ctx->stream)) ||
         (e = cudaStreamSynchronize(ctx->stream)))
         return set_cuda_error(ctx, e, "sequence check");
@@ -284,7 +305,7 @@ int sw_ctx_set_option(sw_ctx *ctx, int option, int64_t value)
     if (!ctx) return SW_EINVAL;
     switch (option) {
     case SW_OPT_ROWS_PER_THREAD:
-        if (!fwd_rpt_supported((int)value)) return SW_EINVAL;
+        if (value != 0 && !fwd_rpt_supported((int)value)) return SW_EINVAL;
         ctx->opt.rows_per_thread = (int)value; return SW_OK;
     case SW_OPT_WARPS_PER_SM:
         if (value < 0 || value > 64) return SW_EINVAL;
@@ -333,9 +354,11 @@ int sw_score(sw_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64_t
     jobs[0] = {da, db, (int32_t)n, (int32_t)m, FWD_LOCAL, 0, 0};
     std::vector<int4> res;
     float ms = 0;
+    const int64_t l0 = ctx->launches;
     st = run_forward(ctx, sc, jobs, !(flags & SW_FLAG_NO_PRUNE), ctx->opt.rows_per_thread, res,
                      &out->stats, &ms);
     out->stats.ms_forward = ms;
+    out->stats.kernel_launches = ctx->launches - l0;
     if (st) return st;
     if (res[0].w && res[0].x > 0) {
         out->score = res[0].x;
@@ -380,6 +403,8 @@ int sw_score_plain(sw_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, i
     cudaEventRecord(ctx->ev[0], strm);
     if ((e = plain_score(da, (int)n, db, (int)m, tab, sc.alphabet, sc.go, sc.ge, bufs, key, strm)))
         return set_cuda_error(ctx, e, "plain launch");
+    out->stats.kernel_launches = n + m - 1;
+    ctx->launches += n + m - 1;
     cudaEventRecord(ctx->ev[1], strm);
     unsigned long long hk = 0;
     if ((e = cudaMemcpyAsync(&hk, key, 8, cudaMemcpyDeviceToHost, strm)) || (e = cudaStreamSynchronize(strm)))

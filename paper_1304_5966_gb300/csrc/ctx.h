@@ -101,7 +101,7 @@ struct SchemeDev {
 };
 
 struct Options {
-    int rows_per_thread = 16;
+    int rows_per_thread = 0;       // 0 = chosen per call from the problem size
     int warps_per_sm = 0;          // 0 = occupancy limit
     int64_t timeout_ms = 2000;
     int fault_band = -1;
@@ -123,6 +123,7 @@ struct sw_ctx {
     std::string last_error;
     cudaEvent_t ev[8] = {};
     std::mutex call_mu;
+    int64_t launches = 0;          // kernels launched by this context (all calls)
 };
 
 namespace swgb {

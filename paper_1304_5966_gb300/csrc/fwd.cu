@@ -95,6 +95,8 @@ __global__ void __launch_bounds__(128) fwd_kernel(const FwdParams P)
         int best = binit, bk = RPT, bc = -1;
         int published = 0;
         unsigned tiles = 0, pruned = 0;
+        unsigned long long cells = 0;
+        const int lane_rows = max(0, min(RPT, n - rowbase));
         bool aborted = false;
 
         const int nch = (m + CH - 1) / CH;
@@ -150,6 +152,11 @@ __global__ void __launch_bounds__(128) fwd_kernel(const FwdParams P)
                 skip = bound < (long long)pthr;
             }
             ++tiles;
+            if (!skip) {
+                // cells this lane really computes in this block (columns in range x rows < n)
+                const int jlo = max(0, q * CH - lane), jhi = min(m, q * CH + CH - lane);
+                if (jhi > jlo) cells += (unsigned long long)(jhi - jlo) * (unsigned)lane_rows;
+            }
             if (skip) {
                 ++pruned;
 #pragma unroll
@@ -258,13 +265,13 @@ __global__ void __launch_bounds__(128) fwd_kernel(const FwdParams P)
             else take = (oc < vc) || (oc == vc && orr < vr);
             if (take) { vs = os; vr = orr; vc = oc; ok = ook; }
         }
+        for (int off = 16; off >= 1; off >>= 1) cells += __shfl_xor_sync(FULL, cells, off);
         if (lane == 0) {
             pr.band_res[band] = make_int4(vs, vr, vc, ok);
             if (anch && ok && vs == target) atomicMin(pr.stop_band, band);
             atomicAdd(&P.stats[1], (unsigned long long)tiles);
             atomicAdd(&P.stats[2], (unsigned long long)pruned);
-            atomicAdd(&P.stats[0], (unsigned long long)(tiles - pruned) * CH *
-                                       (unsigned long long)min(R, rows_left));
+            atomicAdd(&P.stats[0], cells);
         }
     }
 }

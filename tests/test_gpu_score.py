@@ -65,7 +65,7 @@ def test_rows_per_thread_variants(sw, ctx, rpt):
             assert _got(sw, ctx, a, b) == _want(a, b)
             assert _got(sw, ctx, a, b, flags=sw.SW_FLAG_NO_PRUNE) == _want(a, b)
     finally:
-        ctx.set_option(sw.SW_OPT_ROWS_PER_THREAD, 16)
+        ctx.set_option(sw.SW_OPT_ROWS_PER_THREAD, 0)
 
 
 def test_tie_heavy_inputs(sw, ctx):
