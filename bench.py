@@ -47,7 +47,31 @@ def _args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-extras", action="store_true", help="skip the batch / plain comparisons")
+    p.add_argument("--workload", default="pair_5m", choices=["pair_5m", "score_500k"],
+                   help="score_500k: forward pass alone on a 500 kbp homologous pair (profiling case)")
+    p.add_argument("--workspace-gb", type=int, default=0, help="device workspace (default by workload)")
     return p.parse_args()
+
+
+def run_profile_case(args):
+    """Small case for ncu: sw_score on a 500,000 x ~500,000 homologous pair."""
+    import torch
+    import paper_1304_5966_gb300 as sw
+    from gen import synth
+    a, b = synth.pair_homologous(500_000, seed=13, gc_permille=410)
+    ctx = sw.sw_ctx_create(0, workspace_bytes=(args.workspace_gb or 1) << 30)
+    ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    for _ in range(args.warmup):
+        sw.sw_score(ctx, ta, tb)
+    ms = []
+    for _ in range(args.steps):
+        r = sw.sw_score(ctx, ta, tb)
+        ms.append(r.stats["ms_forward"])
+    print(json.dumps({"workload": "score_500k", "n": len(a), "m": len(b), "score": r.score,
+                      "end": [r.a_end, r.b_end], "ms_forward": ms,
+                      "gcups": round(len(a) * len(b) / statistics.mean(ms) / 1e6, 1),
+                      "fwd_cells": r.stats["fwd_cells"], "tiles_pruned": r.stats["tiles_pruned"],
+                      "tiles_total": r.stats["tiles_total"]}), flush=True)
 
 
 def _dist():
@@ -142,6 +166,8 @@ def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "score_500k":
+        return run_profile_case(args)
     ws, rank, local = _dist()
     import numpy as np
     import torch
@@ -156,7 +182,7 @@ def main():
 
     a, b = synth.pair_5m()
     n, m = len(a), len(b)
-    ctx = sw.sw_ctx_create(local, workspace_bytes=24 << 30)
+    ctx = sw.sw_ctx_create(local, workspace_bytes=(args.workspace_gb or 24) << 30)
     stream = ctx.stream
     ta = torch.from_numpy(a).cuda()
     tb = torch.from_numpy(b).cuda()

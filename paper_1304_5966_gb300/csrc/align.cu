@@ -22,23 +22,12 @@
 #include <vector>
 
 #include "common.cuh"
-#include "ctx.h"
+#include "align.h"
 #include "lab.h"
 
 using namespace swgb;
 
 namespace swgb {
-
-int stage_seq(sw_ctx *ctx, Scope &sc, const uint8_t *p, int64_t len, int alph, bool dev_in,
-              const uint8_t **out);
-int validate_lengths(sw_ctx *ctx, int64_t n, int64_t m, const SchemeDev &sc);
-
-struct Sub {
-    int64_t a0, b0;    // offsets into the user's A and B
-    int64_t n, m;      // rows (A) and columns (B)
-    int src, snk;      // user states
-    int64_t S;         // optimum from source to sink
-};
 
 struct Seg {
     bool pending;
@@ -136,7 +125,11 @@ static int run_label_level(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, 
     std::memset(&P, 0, sizeof P);
     P.probs = dprobs; P.tickets = dtk; P.ntickets = (int32_t)ntk; P.ticket_ctr = ctrs; P.err = ctrs + 1;
     P.stats = dstats;
-    for (int x = 0; x < 8; ++x) { P.prof_lo[x] = sc.prof_lo[x]; P.prof_hi[x] = sc.prof_hi[x]; }
+    const bool tr_launch = np > 0 && trans[0];
+    for (int x = 0; x < 8; ++x) {
+        P.prof_lo[x] = tr_launch ? sc.prof_lo_t[x] : sc.prof_lo[x];
+        P.prof_hi[x] = tr_launch ? sc.prof_hi_t[x] : sc.prof_hi[x];
+    }
     P.go = sc.go; P.ge = sc.ge; P.max_sub = sc.max_sub; P.prune = prune ? 1 : 0;
     P.timeout_ns = (unsigned long long)ctx->opt.timeout_ms * 1000000ull;
     const bool p2 = sc.alphabet > 4;
@@ -211,7 +204,7 @@ static int split_sub(const Sub &u, int tr, const std::vector<Crossing> &cr, int 
         Seg e{false, Sub{}, std::string()};
         if (x.type == LAB_DIAG) {
             if (x.r >= kn || x.c >= km) return SW_ECUDA;
-            w = sc.table[ka[x.r] * 8 + kb[x.c]];
+            w = tr ? sc.table[kb[x.c] * 8 + ka[x.r]] : sc.table[ka[x.r] * 8 + kb[x.c]];
             e.ops = "M";
             pr_ = x.r + 1; pc = x.c + 1; pst = ST_H;
         } else {
@@ -266,12 +259,16 @@ static int run_leaves(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const
 
 // Reconstruct the canonical alignment of A[a0, a0+n) x B[b0, b0+m) between
 // H(0,0) and H(n,m) with optimum S.  dA/dB device, hA/hB host copies.
-int reconstruct(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const uint8_t *dB,
-                const uint8_t *hA, const uint8_t *hB, int64_t a0, int64_t n, int64_t b0, int64_t m,
-                int64_t S, bool prune, std::string &ops_out, sw_stats *stats)
+int reconstruct_many(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const uint8_t *dB,
+                     const uint8_t *hA, const uint8_t *hB, const std::vector<Sub> &roots, bool prune,
+                     std::vector<std::string> &ops_out, sw_stats *stats)
 {
     std::vector<Seg> segs;
-    segs.push_back({true, Sub{a0, b0, n, m, ST_H, ST_H, S}, std::string()});
+    std::vector<int> owner;                 // root index of every segment
+    for (size_t r = 0; r < roots.size(); ++r) {
+        segs.push_back({true, roots[r], std::string()});
+        owner.push_back((int)r);
+    }
     const int64_t leaf_cells = ctx->opt.leaf_cells;
     int levels = 0;
     for (;;) {
@@ -339,21 +336,35 @@ int reconstruct(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const uint8
                     }
                 }
             }
+            std::vector<int> next_owner;
             for (int k = 0; k < (int)segs.size(); ++k) {
-                if (!children[k].empty()) for (auto &c : children[k]) next.push_back(std::move(c));
-                else next.push_back(std::move(segs[k]));
+                if (!children[k].empty()) {
+                    for (auto &c : children[k]) { next.push_back(std::move(c)); next_owner.push_back(owner[k]); }
+                } else {
+                    next.push_back(std::move(segs[k]));
+                    next_owner.push_back(owner[k]);
+                }
             }
             segs.swap(next);
+            owner.swap(next_owner);
         }
         if (levels > 200) { ctx->last_error = "internal: reconstruction does not converge"; return SW_ECUDA; }
     }
-    size_t total = 0;
-    for (auto &sg : segs) total += sg.ops.size();
-    ops_out.clear();
-    ops_out.reserve(total);
-    for (auto &sg : segs) ops_out += sg.ops;
-    if (stats) stats->levels = levels;
+    ops_out.assign(roots.size(), std::string());
+    for (size_t k = 0; k < segs.size(); ++k) ops_out[owner[k]] += segs[k].ops;
+    if (stats) stats->levels = std::max(stats->levels, levels);
     return SW_OK;
+}
+
+int reconstruct(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const uint8_t *dB,
+                const uint8_t *hA, const uint8_t *hB, int64_t a0, int64_t n, int64_t b0, int64_t m,
+                int64_t S, bool prune, std::string &ops_out, sw_stats *stats)
+{
+    std::vector<Sub> roots(1, Sub{a0, b0, n, m, ST_H, ST_H, S});
+    std::vector<std::string> ops;
+    const int st = reconstruct_many(ctx, sc, dA, dB, hA, hB, roots, prune, ops, stats);
+    if (st == SW_OK) ops_out.swap(ops[0]);
+    return st;
 }
 
 char *make_cigar(const std::string &ops, const uint8_t *a, const uint8_t *b, int64_t *len_out)

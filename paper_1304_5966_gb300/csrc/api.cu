@@ -7,6 +7,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "align.h"
 #include "ctx.h"
 
 using namespace swgb;
@@ -54,6 +55,11 @@ int build_scheme(const sw_scheme *s, SchemeDev *out)
         for (int y = 0; y < 4; ++y) hi |= (uint32_t)(uint8_t)d.table[x * 8 + 4 + y] << (8 * y);
         d.prof_lo[x] = lo;
         d.prof_hi[x] = hi;
+        uint32_t tlo = 0, thi = 0;
+        for (int y = 0; y < 4; ++y) tlo |= (uint32_t)(uint8_t)d.table[y * 8 + x] << (8 * y);
+        for (int y = 0; y < 4; ++y) thi |= (uint32_t)(uint8_t)d.table[(4 + y) * 8 + x] << (8 * y);
+        d.prof_lo_t[x] = tlo;
+        d.prof_hi_t[x] = thi;
     }
     *out = d;
     return SW_OK;
@@ -85,14 +91,31 @@ static int auto_rpt(sw_ctx *ctx, const std::vector<FwdJob> &jobs, bool p2)
     return 8;
 }
 
-int run_forward(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &jobs, bool prune,
-                int rpt, std::vector<int4> &res, sw_stats *stats, float *ms)
+static int auto_rpt16(sw_ctx *ctx, const std::vector<FwdJob> &jobs)
+{
+    const int cands[3] = {16, 8, 4};
+    for (int k = 0; k < 3; ++k) {
+        int per_sm = 1;
+        if (fwd16_occupancy(cands[k], &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+        const double warps = 4.0 * per_sm * ctx->sms;
+        int64_t bands = 0, rows = 0;
+        for (auto &j : jobs) { bands += (j.n + 64 * cands[k] - 1) / (64 * cands[k]); rows += j.n; }
+        // enough bands to fill the GPU, and not mostly empty rows in the bands
+        if (bands >= 2.0 * warps && (double)rows >= 0.6 * (double)bands * 64 * cands[k]) return cands[k];
+    }
+    return 4;
+}
+
+static int run_forward_impl(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &jobs, bool prune,
+                            int rpt, bool lane16, std::vector<int4> &res, std::vector<int> *ovf,
+                            sw_stats *stats, float *ms)
 {
     const int np = (int)jobs.size();
     res.assign(np, make_int4(0, 0, 0, 0));
+    if (ovf) ovf->assign(np, 0);
     if (np == 0) return SW_OK;
-    if (rpt <= 0) rpt = auto_rpt(ctx, jobs, sc.alphabet > 4);
-    const int R = 32 * rpt;
+    if (rpt <= 0) rpt = lane16 ? auto_rpt16(ctx, jobs) : auto_rpt(ctx, jobs, sc.alphabet > 4);
+    const int R = (lane16 ? 64 : 32) * rpt;
     Scope sc_(ctx->arena);
     std::vector<FwdProblem> hp(np);
     int64_t ntk = 0;
@@ -161,20 +184,38 @@ int run_forward(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &job
     P.ticket_ctr = ctrs;
     P.err = ctrs + 1;
     P.stats = dstats;
-    for (int x = 0; x < 8; ++x) { P.prof_lo[x] = sc.prof_lo[x]; P.prof_hi[x] = sc.prof_hi[x]; }
+    for (int x = 0; x < 8; ++x) {
+        P.prof_lo[x] = sc.prof_lo[x]; P.prof_hi[x] = sc.prof_hi[x];
+        P.prof_lo_t[x] = sc.prof_lo_t[x]; P.prof_hi_t[x] = sc.prof_hi_t[x];
+    }
     P.go = sc.go; P.ge = sc.ge; P.max_sub = sc.max_sub;
     P.prune = prune ? 1 : 0;
     P.fault_band = ctx->opt.fault_band;
     P.timeout_ns = (unsigned long long)ctx->opt.timeout_ms * 1000000ull;
     const bool p2 = sc.alphabet > 4;
-    int ctas = occupancy_ctas(ctx, rpt, p2);
+    int ctas;
+    if (lane16) {
+        int per_sm = 1;
+        if (fwd16_occupancy(rpt, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+        if (ctx->opt.warps_per_sm > 0) per_sm = std::max(1, std::min(per_sm, ctx->opt.warps_per_sm / 4));
+        ctas = per_sm * ctx->sms;
+    } else {
+        ctas = occupancy_ctas(ctx, rpt, p2);
+    }
     ctas = (int)std::min<int64_t>(ctas, (ntk + 3) / 4);
     cudaEventRecord(ctx->ev[0], s);
-    if ((e = fwd_launch(P, rpt, p2, ctas, 128, s))) return set_cuda_error(ctx, e, "forward launch");
+    if ((e = lane16 ? fwd16_launch(P, rpt, ctas, s) : fwd_launch(P, rpt, p2, ctas, 128, s)))
+        return set_cuda_error(ctx, e, "forward launch");
     cudaEventRecord(ctx->ev[1], s);
     if ((e = fwd_reduce_launch(dprobs, np, dres, s))) return set_cuda_error(ctx, e, "forward reduce");
     int32_t herr = 0;
     unsigned long long hst[4];
+    std::vector<int32_t> hctr;
+    if (ovf) {
+        hctr.resize(3 * (size_t)np);
+        if ((e = cudaMemcpyAsync(hctr.data(), ctrs + 8, sizeof(int32_t) * 3 * np, cudaMemcpyDeviceToHost, s)))
+            return set_cuda_error(ctx, e, "forward overflow words");
+    }
     if ((e = cudaMemcpyAsync(res.data(), dres, sizeof(int4) * np, cudaMemcpyDeviceToHost, s)) ||
         (e = cudaMemcpyAsync(&herr, ctrs + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) ||
         (e = cudaMemcpyAsync(hst, dstats, sizeof hst, cudaMemcpyDeviceToHost, s)) ||
@@ -190,7 +231,21 @@ int run_forward(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &job
     }
     if (herr == DEV_ETIMEOUT) { ctx->last_error = "device-side inter-band wait timed out"; return SW_ETIMEOUT; }
     if (herr) { ctx->last_error = "device error word set"; return SW_ECUDA; }
+    if (ovf)
+        for (int p = 0; p < np; ++p) (*ovf)[p] = hctr[3 * (size_t)p + 2] != 0;
     return SW_OK;
+}
+
+int run_forward(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &jobs, bool prune,
+                int rpt, std::vector<int4> &res, sw_stats *stats, float *ms)
+{
+    return run_forward_impl(ctx, sc, jobs, prune, rpt, false, res, nullptr, stats, ms);
+}
+
+int run_forward16(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &jobs, bool prune,
+                  int rpt, std::vector<int4> &res, std::vector<int> &ovf, sw_stats *stats, float *ms)
+{
+    return run_forward_impl(ctx, sc, jobs, prune, rpt, true, res, &ovf, stats, ms);
 }
 
 // copy (or borrow) a sequence to the device and check its codes

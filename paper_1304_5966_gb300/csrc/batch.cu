@@ -1,9 +1,229 @@
-// batch.cu -- sw_align_batch: many pairs in one persistent launch.
-#include "ctx.h"
+// batch.cu -- sw_align_batch: many independent pairs per launch.
+//
+// All pairs' row bands go into one ordered ticket queue of a persistent kernel
+// (fwd.cu / fwd16.cu), so thousands of pairs of very different lengths share the
+// GPU without a launch per pair; within a pair the bands still form the
+// wavefront pipeline.  Each pair is oriented so that its longer sequence indexes
+// the rows (fewer column steps on the critical path; the tie rule follows the
+// orientation so results are in the user's row-major order).  Pairs whose score
+// bound fits int16 run on int16x2 lanes (two cells per instruction); a pair
+// whose values reach the int16 guard is re-run on int32 lanes.  Alignment
+// requests then run their start-point passes as one batched anchored launch and
+// their reconstructions as one recursion over all pairs.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
 
-extern "C" int sw_align_batch(sw_ctx *ctx, const sw_pair *, int32_t, const sw_scheme *, int32_t,
-                              sw_result *outs)
+#include "align.h"
+#include "common.cuh"
+#include "lab.h"
+
+using namespace swgb;
+
+namespace swgb {
+
+// can this pair run on int16x2 lanes without possible overflow?
+static bool fits_int16(const SchemeDev &sc, int64_t n, int64_t m)
 {
-    if (!ctx || !outs) return SW_EINVAL;
-    return SW_ENOTIMPL;
+    if (sc.alphabet > 4) return false;
+    if (sc.go + sc.ge + 128 >= 32768) return false;
+    const int64_t bound = (int64_t)sc.max_sub * std::min(n, m);
+    return bound < 32767 - 2 * sc.max_sub;
+}
+
+int batch_forward(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const uint8_t *dB,
+                  const std::vector<int64_t> &aoff, const std::vector<int64_t> &boff,
+                  const std::vector<int64_t> &len_a, const std::vector<int64_t> &len_b, int32_t flags,
+                  std::vector<int4> &score_end, sw_stats *stats, float *ms_total)
+{
+    const int count = (int)len_a.size();
+    score_end.assign(count, make_int4(0, -1, -1, 0));
+    const bool prune = !(flags & SW_FLAG_NO_PRUNE);
+    std::vector<FwdJob> j16, j32;
+    std::vector<int> id16, id32;
+    std::vector<int> trans(count, 0);
+    for (int p = 0; p < count; ++p) {
+        const int64_t n = len_a[p], m = len_b[p];
+        if (n == 0 || m == 0) continue;
+        const int t = m > n ? 1 : 0;
+        trans[p] = t;
+        FwdJob j;
+        j.a = t ? dB + boff[p] : dA + aoff[p];
+        j.b = t ? dA + aoff[p] : dB + boff[p];
+        j.n = (int32_t)(t ? m : n);
+        j.m = (int32_t)(t ? n : m);
+        j.mode = FWD_LOCAL; j.target = 0; j.transposed = t;
+        const bool use16 = !(flags & SW_FLAG_FORCE_INT32) && sc.alphabet <= 4 &&
+                           ((flags & SW_FLAG_FORCE_INT16) || fits_int16(sc, n, m));
+        if (use16) { j16.push_back(j); id16.push_back(p); }
+        else { j32.push_back(j); id32.push_back(p); }
+    }
+    auto store = [&](int p, const int4 &r) {
+        if (!r.w || r.x <= 0) { score_end[p] = make_int4(0, -1, -1, 1); return; }
+        // kernel (row, col) -> user (a_end, b_end)
+        if (trans[p]) score_end[p] = make_int4(r.x, r.z, r.y, 1);
+        else score_end[p] = make_int4(r.x, r.y, r.z, 1);
+    };
+    float ms = 0, ms2 = 0;
+    int st;
+    if (!j16.empty()) {
+        std::vector<int4> res;
+        std::vector<int> ovf;
+        if ((st = run_forward16(ctx, sc, j16, prune, 0, res, ovf, stats, &ms))) return st;
+        for (size_t k = 0; k < j16.size(); ++k) {
+            if (ovf[k]) { j32.push_back(j16[k]); id32.push_back(id16[k]); if (stats) stats->int16_reruns++; }
+            else store(id16[k], res[k]);
+        }
+    }
+    if (!j32.empty()) {
+        std::vector<int4> res;
+        if ((st = run_forward(ctx, sc, j32, prune, 0, res, stats, &ms2))) return st;
+        for (size_t k = 0; k < j32.size(); ++k) store(id32[k], res[k]);
+    }
+    if (ms_total) *ms_total = ms + ms2;
+    return SW_OK;
+}
+
+}  // namespace swgb
+
+extern "C" int sw_align_batch(sw_ctx *ctx, const sw_pair *pairs, int32_t count, const sw_scheme *scheme,
+                              int32_t flags, sw_result *outs)
+{
+    if (!ctx || !outs || count < 0 || (count > 0 && !pairs)) return SW_EINVAL;
+    for (int p = 0; p < count; ++p) {
+        std::memset(&outs[p], 0, sizeof(sw_result));
+        outs[p].a_begin = outs[p].a_end = outs[p].b_begin = outs[p].b_end = -1;
+    }
+    if (count == 0) return SW_OK;
+    std::lock_guard<std::mutex> g(ctx->call_mu);
+    SchemeDev sc;
+    int st = build_scheme(scheme, &sc);
+    if (st) { ctx->last_error = "invalid scheme"; return st; }
+    const bool dev = (flags & SW_FLAG_DEVICE_INPUT) != 0;
+    const bool score_only = (flags & SW_FLAG_SCORE_ONLY) != 0;
+    std::vector<int64_t> la(count), lb(count), aoff(count), boff(count);
+    int64_t ta = 0, tb = 0;
+    for (int p = 0; p < count; ++p) {
+        if ((st = validate_lengths(ctx, pairs[p].n, pairs[p].m, sc))) return st;
+        if ((pairs[p].n && !pairs[p].a) || (pairs[p].m && !pairs[p].b)) return SW_EINVAL;
+        la[p] = pairs[p].n; lb[p] = pairs[p].m;
+        aoff[p] = ta; boff[p] = tb;
+        ta += la[p]; tb += lb[p];
+        outs[p].stats.cells = la[p] * lb[p];
+    }
+    cudaSetDevice(ctx->device);
+    const int64_t l0 = ctx->launches;
+    Scope s(ctx->arena);
+    uint8_t *dA = s.get<uint8_t>((size_t)ta + 16), *dB = s.get<uint8_t>((size_t)tb + 16);
+    if (s.failed()) { ctx->last_error = "workspace too small for the batch sequences"; return SW_ENOMEM; }
+    std::vector<uint8_t> hA((size_t)ta), hB((size_t)tb);
+    cudaError_t e;
+    if (!dev) {
+        for (int p = 0; p < count; ++p) {
+            if (la[p]) std::memcpy(hA.data() + aoff[p], pairs[p].a, (size_t)la[p]);
+            if (lb[p]) std::memcpy(hB.data() + boff[p], pairs[p].b, (size_t)lb[p]);
+        }
+        for (int64_t i = 0; i < ta; ++i) if (hA[i] >= sc.alphabet) { ctx->last_error = "sequence code >= alphabet"; return SW_EINVAL; }
+        for (int64_t i = 0; i < tb; ++i) if (hB[i] >= sc.alphabet) { ctx->last_error = "sequence code >= alphabet"; return SW_EINVAL; }
+        if ((e = cudaMemcpyAsync(dA, hA.data(), (size_t)ta, cudaMemcpyHostToDevice, ctx->stream)) ||
+            (e = cudaMemcpyAsync(dB, hB.data(), (size_t)tb, cudaMemcpyHostToDevice, ctx->stream)))
+            return set_cuda_error(ctx, e, "batch upload");
+    } else {
+        for (int p = 0; p < count; ++p) {
+            if ((la[p] && (e = cudaMemcpyAsync(dA + aoff[p], pairs[p].a, (size_t)la[p], cudaMemcpyDeviceToDevice, ctx->stream))) ||
+                (lb[p] && (e = cudaMemcpyAsync(dB + boff[p], pairs[p].b, (size_t)lb[p], cudaMemcpyDeviceToDevice, ctx->stream))))
+                return set_cuda_error(ctx, e, "batch gather");
+        }
+        const uint8_t *chk;
+        if ((st = stage_seq(ctx, s, dA, ta, sc.alphabet, true, &chk))) return st;
+        if ((st = stage_seq(ctx, s, dB, tb, sc.alphabet, true, &chk))) return st;
+        if (!score_only) {
+            if ((e = cudaMemcpyAsync(hA.data(), dA, (size_t)ta, cudaMemcpyDeviceToHost, ctx->stream)) ||
+                (e = cudaMemcpyAsync(hB.data(), dB, (size_t)tb, cudaMemcpyDeviceToHost, ctx->stream)) ||
+                (e = cudaStreamSynchronize(ctx->stream)))
+                return set_cuda_error(ctx, e, "batch readback");
+        }
+    }
+    sw_stats agg{};
+    std::vector<int4> se;
+    float ms = 0;
+    if ((st = batch_forward(ctx, sc, dA, dB, aoff, boff, la, lb, flags, se, &agg, &ms))) return st;
+    for (int p = 0; p < count; ++p) {
+        if (se[p].x > 0) { outs[p].score = se[p].x; outs[p].a_end = se[p].y; outs[p].b_end = se[p].z; }
+        outs[p].stats.int16_reruns = 0;
+    }
+    outs[0].stats.ms_forward = ms;
+    outs[0].stats.fwd_cells = agg.fwd_cells;
+    outs[0].stats.cells_computed = agg.cells_computed;
+    outs[0].stats.tiles_total = agg.tiles_total;
+    outs[0].stats.tiles_pruned = agg.tiles_pruned;
+    outs[0].stats.int16_reruns = agg.int16_reruns;
+    if (!score_only) {
+        const bool prune = !(flags & SW_FLAG_NO_PRUNE);
+        // start points: one anchored launch over all reversed prefixes
+        std::vector<int> ids;
+        int64_t ra = 0, rbt = 0;
+        for (int p = 0; p < count; ++p)
+            if (se[p].x > 0) { ids.push_back(p); ra += se[p].y; rbt += se[p].z; }
+        if (!ids.empty()) {
+            const int k = (int)ids.size();
+            Scope s2(ctx->arena);
+            uint8_t *rA = s2.get<uint8_t>((size_t)ra + 16), *rB = s2.get<uint8_t>((size_t)rbt + 16);
+            int64_t *offs = s2.get<int64_t>(4 * (size_t)k);
+            int32_t *lens = s2.get<int32_t>(2 * (size_t)k);
+            if (s2.failed()) { ctx->last_error = "workspace too small for the start passes"; return SW_ENOMEM; }
+            std::vector<int64_t> ho(4 * (size_t)k);
+            std::vector<int32_t> hl(2 * (size_t)k);
+            int64_t pa = 0, pb = 0;
+            for (int x = 0; x < k; ++x) {
+                const int p = ids[x];
+                ho[x] = aoff[p]; ho[k + x] = pa; hl[x] = se[p].y;
+                ho[2 * k + x] = boff[p]; ho[3 * k + x] = pb; hl[k + x] = se[p].z;
+                pa += se[p].y; pb += se[p].z;
+            }
+            if ((e = cudaMemcpyAsync(offs, ho.data(), sizeof(int64_t) * ho.size(), cudaMemcpyHostToDevice, ctx->stream)) ||
+                (e = cudaMemcpyAsync(lens, hl.data(), sizeof(int32_t) * hl.size(), cudaMemcpyHostToDevice, ctx->stream)) ||
+                (e = reverse_segments_launch(dA, rA, offs, offs + k, lens, k, ctx->stream)) ||
+                (e = reverse_segments_launch(dB, rB, offs + 2 * k, offs + 3 * k, lens + k, k, ctx->stream)))
+                return set_cuda_error(ctx, e, "batch reverse");
+            ctx->launches += 2;
+            std::vector<FwdJob> jobs(k);
+            for (int x = 0; x < k; ++x) {
+                const int p = ids[x];
+                jobs[x] = {rA + ho[k + x], rB + ho[3 * k + x], se[p].y, se[p].z, FWD_ANCHORED, BIAS + se[p].x, 0};
+            }
+            std::vector<int4> res;
+            float ms_s = 0;
+            sw_stats tmp{};
+            if ((st = run_forward(ctx, sc, jobs, prune, 0, res, &tmp, &ms_s))) return st;
+            outs[0].stats.ms_start = ms_s;
+            std::vector<Sub> roots(k);
+            for (int x = 0; x < k; ++x) {
+                const int p = ids[x];
+                if (!res[x].w || res[x].x != BIAS + se[p].x) { ctx->last_error = "internal: start point not found"; return SW_ECUDA; }
+                outs[p].a_begin = se[p].y - res[x].y;
+                outs[p].b_begin = se[p].z - res[x].z;
+                roots[x] = Sub{aoff[p] + outs[p].a_begin, boff[p] + outs[p].b_begin,
+                               outs[p].a_end - outs[p].a_begin, outs[p].b_end - outs[p].b_begin, ST_H, ST_H,
+                               (int64_t)se[p].x};
+            }
+            std::vector<std::string> ops;
+            cudaEventRecord(ctx->ev[5], ctx->stream);
+            if ((st = reconstruct_many(ctx, sc, dA, dB, hA.data(), hB.data(), roots, prune, ops, &outs[0].stats)))
+                return st;
+            cudaEventRecord(ctx->ev[6], ctx->stream);
+            cudaEventSynchronize(ctx->ev[6]);
+            cudaEventElapsedTime(&outs[0].stats.ms_align, ctx->ev[5], ctx->ev[6]);
+            for (int x = 0; x < k; ++x) {
+                const int p = ids[x];
+                int64_t cl = 0;
+                outs[p].cigar = make_cigar(ops[x], hA.data() + roots[x].a0, hB.data() + roots[x].b0, &cl);
+                if (!outs[p].cigar) return SW_ENOMEM;
+                outs[p].cigar_len = cl;
+            }
+        }
+    }
+    outs[0].stats.kernel_launches = ctx->launches - l0;
+    return SW_OK;
 }

@@ -98,6 +98,7 @@ struct SchemeDev {
     int min_sub = -3;
     int8_t table[64];          // 8 x 8 row-major (a code, b code)
     uint32_t prof_lo[8], prof_hi[8];
+    uint32_t prof_lo_t[8], prof_hi_t[8];   // same for the transposed table
 };
 
 struct Options {

@@ -76,8 +76,8 @@ __global__ void __launch_bounds__(128) fwd_kernel(const FwdParams P)
             uint32_t lo = VIRTUAL_PROF, hi = VIRTUAL_PROF;
             if (r < n) {
                 const int c = pr.a[r] & 7;
-                lo = P.prof_lo[c];
-                if (PROF2) hi = P.prof_hi[c];
+                lo = transposed ? P.prof_lo_t[c] : P.prof_lo[c];
+                if (PROF2) hi = transposed ? P.prof_hi_t[c] : P.prof_hi[c];
             }
             plo[k] = lo;
             phi[k] = PROF2 ? hi : 0u;

@@ -1,0 +1,330 @@
+// fwd16.cu -- forward local pass on int16x2 lanes (sm_103a DPX 16x2 forms).
+//
+// Same computation and tie rule as fwd.cu (FWD_LOCAL), with two cells per
+// register: a warp owns a band of 64*RPT rows, lane t holds the rows of
+// "virtual lane" t in the low halfword and of virtual lane t+32 in the high
+// halfword of every state register.  Virtual lane v processes column j at step
+// j + v, so the high half runs 32 columns behind the low half.  Each step the
+// bottom row of every virtual lane moves to the next one by a rotating shuffle
+// (lane 0's high half receives lane 31's low half); lane 0's low half reads the
+// row above the band from the shared-memory chunk, lane 31's high half writes
+// the band's bottom row.  Scores are absolute int16: the host routes a pair here
+// only when max_sub * min(n, m) and the gap costs stay inside int16, and a value
+// reaching the guard (32767 - max_sub) sets the problem's overflow word so the
+// pair is re-run on int32 lanes (the first value to reach the guard is computed
+// before anything can wrap, since H grows by at most max_sub per step).
+//
+// Per cell pair: prmt (both substitution scores), viaddmax16x2 (F),
+// viaddmax16x2 (diag + s vs E), vimax3_16x2 (with F and the zero floor),
+// viaddmax16x2 (H - go), viaddmax16x2 (E), and half a vimax3_16x2 for the
+// running maximum.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace swgb {
+
+__device__ __forceinline__ uint32_t p16(int lo, int hi) {
+    return ((uint32_t)lo & 0xffffu) | ((uint32_t)hi << 16);
+}
+__device__ __forceinline__ int lo16(uint32_t x) { return (int)(int16_t)(x & 0xffffu); }
+__device__ __forceinline__ int hi16(uint32_t x) { return (int)(int16_t)(x >> 16); }
+__device__ __forceinline__ uint32_t perm(uint32_t a, uint32_t b, uint32_t s) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(s));
+    return r;
+}
+// selector of a column code for the low half (bytes 0-3 of the profile pair);
+// the high half's selector is the same plus 0x44 (bytes 4-7)
+__device__ __forceinline__ uint32_t sel_lo8(uint32_t c) { return c | ((c | 8u) << 4); }
+
+template <int RPT>
+__global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
+{
+    __shared__ int4 s_in_all[4][3][CH];   // {H, F, selector8, 0} per column, three chunks
+    __shared__ int2 s_out_all[4][2 * CH];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    int4 (*s_in)[CH] = s_in_all[wid];
+    int2 *s_out = s_out_all[wid];
+    const int go = P.go, ge = P.ge;
+    const uint32_t go2 = p16(-go, -go), ge2 = p16(-ge, -ge);
+    const uint32_t NEG2 = p16(-32768, -32768), ZERO2 = 0u;
+    const int src_lane = (lane + 31) & 31;
+    constexpr int R = 64 * RPT;
+
+    for (;;) {
+        int tk = 0, stop_now = 0;
+        if (lane == 0) { tk = atomicAdd(P.ticket_ctr, 1); stop_now = ld_volatile(P.err); }
+        tk = __shfl_sync(FULL, tk, 0);
+        stop_now = __shfl_sync(FULL, stop_now, 0);
+        if (tk >= P.ntickets || stop_now) return;
+        const int2 tb = P.tickets[tk];
+        const FwdProblem &pr = P.probs[tb.x];
+        const int band = tb.y;
+        const int n = pr.n, m = pr.m;
+        const bool transposed = pr.transposed != 0;
+        const uint8_t *__restrict__ bseq = pr.b;
+        int2 *__restrict__ bus = pr.bus;
+        int *__restrict__ flags = pr.flags;
+        const int need = band - 1;
+        const int guard = 32767 - P.max_sub;
+
+        const int rb_lo = band * R + lane * RPT;           // first row of the low half
+        const int rb_hi = rb_lo + 32 * RPT;                // first row of the high half
+        uint32_t plo[RPT], phi[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int r0 = rb_lo + k, r1 = rb_hi + k;
+            const uint32_t *prof = transposed ? P.prof_lo_t : P.prof_lo;
+            plo[k] = (r0 < n) ? prof[pr.a[r0] & 7] : VIRTUAL_PROF;
+            phi[k] = (r1 < n) ? prof[pr.a[r1] & 7] : VIRTUAL_PROF;
+        }
+        const uint32_t EB2 = go2;                          // E(i, 0) = -go (local)
+        uint32_t Hl[RPT], E[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) { Hl[k] = ZERO2; E[k] = EB2; }
+        uint32_t Hlast = ZERO2, Flast = go2, sellast = 0, updiag = ZERO2;
+        int best_lo = 0, bk_lo = RPT, bc_lo = -1, best_hi = 0, bk_hi = RPT, bc_hi = -1;
+        uint32_t thr = p16(1, 1);                          // report values >= max(best, 1)
+        int published = 0;
+        unsigned tiles = 0, pruned = 0;
+        unsigned long long cells = 0;
+        const int rows_lo = max(0, min(RPT, n - rb_lo)), rows_hi = max(0, min(RPT, n - rb_hi));
+        bool aborted = false;
+        const int nch = (m + CH - 1) / CH;
+        const int nblk = nch + 2;
+        const int rows_left = n - band * R;
+        {
+            int ok = 1;
+            if (lane == 0) ok = wait_flag(&flags[0], need, P.err, nullptr, 0, P.timeout_ns);
+            ok = __shfl_sync(FULL, ok, 0);
+            if (!ok) aborted = true;
+            else {
+                int2 v = make_int2(0, -go);
+                uint32_t sel = 0;
+                if (lane < m) { v = bus[lane]; sel = sel_lo8(bseq[lane]); }
+                s_in[0][lane] = make_int4(v.x, v.y, (int)sel, 0);
+            }
+            __syncwarp();
+        }
+        for (int q = 0; q < nblk && !aborted; ++q) {
+            const int buf = q % 3;
+            const bool has_next = (q + 1) < nch;
+            int ready = 0;
+            int2 nv = make_int2(0, -go);
+            uint32_t nsel = 0;
+            const int ncol = (q + 1) * CH + lane;
+            if (has_next) {
+                if (lane == 0) ready = ld_acquire(&flags[q + 1]) >= need;
+                ready = __shfl_sync(FULL, ready, 0);
+                if (ready && ncol < m) { nv = bus[ncol]; nsel = sel_lo8(bseq[ncol]); }
+            }
+            bool skip = false;
+            if (P.prune) {
+                int pthr = 0;
+                if (lane == 0) pthr = ld_volatile(pr.best);
+                pthr = __shfl_sync(FULL, pthr, 0);
+                uint32_t mx2 = Hlast;
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) mx2 = __vimax_s16x2_relu(mx2, Hl[k]);
+                mx2 = __vimax_s16x2_relu(mx2, updiag);
+                int mx = max(lo16(mx2), hi16(mx2));
+                if (q < nch) mx = max(mx, s_in[buf][lane].x);
+                mx = __reduce_max_sync(FULL, mx);
+                const int jmin = max(0, q * CH - 2 * CH);
+                const long long rem = (long long)min(rows_left, m - jmin) + 1;
+                skip = (long long)mx + (long long)P.max_sub * rem < (long long)pthr;
+            }
+            ++tiles;
+            const bool ramp = (q * CH < 2 * CH) || (q * CH + CH - 1 >= m);
+            if (!skip) {
+                int jl = max(0, q * CH - lane), jh = min(m, q * CH + CH - lane);
+                if (jh > jl) cells += (unsigned long long)(jh - jl) * (unsigned)rows_lo;
+                jl = max(0, q * CH - lane - 32); jh = min(m, q * CH + CH - lane - 32);
+                if (jh > jl) cells += (unsigned long long)(jh - jl) * (unsigned)rows_hi;
+            }
+            if (skip) {
+                ++pruned;
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) { Hl[k] = ZERO2; E[k] = EB2; }
+                Hlast = ZERO2;
+                Flast = go2;
+                // selectors of the columns each half reaches at the end of the block
+                const uint32_t s_lo = (q < nch) ? (uint32_t)s_in[buf][31 - lane].z : 0u;
+                const uint32_t s_hi = (q >= 1 && q - 1 < nch) ? (uint32_t)s_in[(q + 2) % 3][31 - lane].z : 0u;
+                sellast = s_lo | ((s_hi + 0x44u) << 8);
+                updiag = (lane == 0 && q < nch) ? p16(s_in[buf][31].x, 0) : ZERO2;
+                const int oc = q * CH - 63 + lane;
+                if (oc >= 0 && oc < m) s_out[oc & 63] = make_int2(0, -go);
+            } else {
+#pragma unroll 1
+                for (int u = 0; u < CH; ++u) {
+                    const int s = q * CH + u;
+                    const int4 in = s_in[buf][u];
+                    const uint32_t rH = __shfl_sync(FULL, Hlast, src_lane);
+                    const uint32_t rF = __shfl_sync(FULL, Flast, src_lane);
+                    const uint32_t rS = __shfl_sync(FULL, sellast, src_lane);
+                    uint32_t upH = rH, upF = rF, sel = rS;
+                    if (lane == 0) {
+                        upH = perm(rH, (uint32_t)in.x, 0x1054u);
+                        upF = perm(rF, (uint32_t)in.y, 0x1054u);
+                        // past the last input chunk the low half is outside the matrix
+                        // (and merged back); mask so stale shared memory cannot reach the
+                        // high half's selector
+                        sel = ((uint32_t)in.z & 0xffu) | (((rS & 0xffu) + 0x44u) << 8);
+                    }
+                    uint32_t diag = updiag;
+                    updiag = upH;
+                    const int jlo = s - lane, jhi = s - lane - 32;
+                    const bool vlo = (unsigned)jlo < (unsigned)m, vhi = (unsigned)jhi < (unsigned)m;
+                    if (vlo || vhi) {
+                        const bool partial = ramp && !(vlo && vhi);
+                        // partial steps keep the half whose column is outside the matrix
+                        const uint32_t ks = vlo ? 0x7610u : 0x3254u;
+                        const uint32_t oFlast = Flast;
+                        uint32_t hgo = __viaddmax_s16x2(upH, go2, NEG2);   // H(i-1, j) - go
+                        uint32_t F = upF;
+                        uint32_t smax = ZERO2;
+                        if (!partial) {
+#pragma unroll
+                            for (int k = 0; k < RPT; ++k) {
+                                const uint32_t sc = perm(plo[k], phi[k], sel);
+                                F = __viaddmax_s16x2(F, ge2, hgo);                     // F(i, j)
+                                const uint32_t t = __viaddmax_s16x2(diag, sc, E[k]);   // max(diag + s, E)
+                                const uint32_t h = __vimax3_s16x2_relu(t, F, ZERO2);   // H(i, j)
+                                diag = Hl[k];
+                                Hl[k] = h;
+                                hgo = __viaddmax_s16x2(h, go2, NEG2);
+                                E[k] = __viaddmax_s16x2(E[k], ge2, hgo);               // E(i, j+1)
+                                smax = __vimax_s16x2_relu(smax, h);
+                            }
+                            Hlast = Hl[RPT - 1];
+                            Flast = F;
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < RPT; ++k) {
+                                const uint32_t sc = perm(plo[k], phi[k], sel);
+                                F = __viaddmax_s16x2(F, ge2, hgo);
+                                const uint32_t t = __viaddmax_s16x2(diag, sc, E[k]);
+                                const uint32_t h = __vimax3_s16x2_relu(t, F, ZERO2);
+                                diag = Hl[k];
+                                Hl[k] = perm(h, Hl[k], ks);
+                                hgo = __viaddmax_s16x2(h, go2, NEG2);
+                                E[k] = perm(__viaddmax_s16x2(E[k], ge2, hgo), E[k], ks);
+                                smax = __vimax_s16x2_relu(smax, h);
+                            }
+                            smax = perm(smax, 0u, ks);
+                            Hlast = Hl[RPT - 1];
+                            Flast = perm(F, oFlast, ks);
+                        }
+                        bool ph, pl;
+                        __vibmax_s16x2(smax, thr, &ph, &pl);
+                        if (ph || pl) {
+                            const int sl = lo16(smax), sh = hi16(smax);
+                            if (pl && vlo) {
+                                int kf = RPT;
+#pragma unroll
+                                for (int k = RPT - 1; k >= 0; --k) if (lo16(Hl[k]) == sl) kf = k;
+                                if (sl > best_lo || (!transposed && kf < bk_lo)) { best_lo = sl; bk_lo = kf; bc_lo = jlo; }
+                            }
+                            if (ph && vhi) {
+                                int kf = RPT;
+#pragma unroll
+                                for (int k = RPT - 1; k >= 0; --k) if (hi16(Hl[k]) == sh) kf = k;
+                                if (sh > best_hi || (!transposed && kf < bk_hi)) { best_hi = sh; bk_hi = kf; bc_hi = jhi; }
+                            }
+                            thr = p16(max(best_lo, 1), max(best_hi, 1));
+                            if (max(best_lo, best_hi) >= guard && pr.ovf) atomicExch(pr.ovf, 1);
+                        }
+                        if (lane == 31 && vhi) s_out[jhi & 63] = make_int2(hi16(Hlast), hi16(Flast));
+                    }
+                    sellast = sel;
+                }
+            }
+            if (has_next) {
+                if (!ready) {
+                    int ok = 1;
+                    if (lane == 0) ok = wait_flag(&flags[q + 1], need, P.err, nullptr, 0, P.timeout_ns);
+                    ok = __shfl_sync(FULL, ok, 0);
+                    if (!ok) { aborted = true; break; }
+                    if (ncol < m) { nv = bus[ncol]; nsel = sel_lo8(bseq[ncol]); }
+                }
+                s_in[(q + 1) % 3][lane] = make_int4(nv.x, nv.y, (int)nsel, 0);
+            }
+            __syncwarp();
+            if (q >= 2) {
+                const int col = (q - 2) * CH + lane;
+                if (col < m) bus[col] = s_out[col & 63];
+                __syncwarp();
+                if (lane == 0 && band != P.fault_band) st_release(&flags[q - 2], band);
+            }
+            const int wb = __reduce_max_sync(FULL, max(best_lo, best_hi));
+            if (lane == 0 && wb > published) { atomicMax(pr.best, wb); published = wb; }
+        }
+        if (aborted) continue;
+        // band result over the 64 virtual lanes (low halves hold the smaller rows)
+        int vs = best_lo, vr = rb_lo + (bk_lo < RPT ? bk_lo : 0) + 1, vc = bc_lo + 1, ok = best_lo > 0;
+        {
+            const int hs = best_hi, hr = rb_hi + (bk_hi < RPT ? bk_hi : 0) + 1, hc = bc_hi + 1, hok = best_hi > 0;
+            bool take;
+            if (!hok) take = false;
+            else if (!ok) take = true;
+            else if (hs != vs) take = hs > vs;
+            else if (!transposed) take = (hr < vr) || (hr == vr && hc < vc);
+            else take = (hc < vc) || (hc == vc && hr < vr);
+            if (take) { vs = hs; vr = hr; vc = hc; ok = hok; }
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            const int os = __shfl_xor_sync(FULL, vs, off);
+            const int orr = __shfl_xor_sync(FULL, vr, off);
+            const int oc = __shfl_xor_sync(FULL, vc, off);
+            const int ook = __shfl_xor_sync(FULL, ok, off);
+            bool take;
+            if (!ook) take = false;
+            else if (!ok) take = true;
+            else if (os != vs) take = os > vs;
+            else if (!transposed) take = (orr < vr) || (orr == vr && oc < vc);
+            else take = (oc < vc) || (oc == vc && orr < vr);
+            if (take) { vs = os; vr = orr; vc = oc; ok = ook; }
+        }
+        for (int off = 16; off >= 1; off >>= 1) cells += __shfl_xor_sync(FULL, cells, off);
+        if (lane == 0) {
+            pr.band_res[band] = make_int4(vs, vr, vc, ok);
+            atomicAdd(&P.stats[1], (unsigned long long)tiles);
+            atomicAdd(&P.stats[2], (unsigned long long)pruned);
+            atomicAdd(&P.stats[0], cells);
+        }
+    }
+}
+
+template <int RPT>
+static cudaError_t launch16(const FwdParams &p, int ctas, cudaStream_t s)
+{
+    fwd16_kernel<RPT><<<ctas, 128, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+bool fwd16_rpt_supported(int rpt) { return rpt == 4 || rpt == 8 || rpt == 16; }
+
+cudaError_t fwd16_launch(const FwdParams &p, int rpt, int ctas, cudaStream_t s)
+{
+    switch (rpt) {
+    case 4: return launch16<4>(p, ctas, s);
+    case 8: return launch16<8>(p, ctas, s);
+    case 16: return launch16<16>(p, ctas, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t fwd16_occupancy(int rpt, int *n)
+{
+    switch (rpt) {
+    case 4: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<4>, 128, 0);
+    case 8: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<8>, 128, 0);
+    case 16: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<16>, 128, 0);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace swgb

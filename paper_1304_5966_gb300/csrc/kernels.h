@@ -35,6 +35,8 @@ struct FwdParams {
     unsigned long long *stats;   // [0] cells computed, [1] tiles, [2] tiles pruned
     uint32_t prof_lo[8];     // per a-code: s(a, c) for c = 0..3 as signed bytes
     uint32_t prof_hi[8];     // per a-code: s(a, c) for c = 4..7
+    uint32_t prof_lo_t[8];   // the same for transposed problems: s(c, a)
+    uint32_t prof_hi_t[8];
     int32_t go, ge, max_sub;
     int32_t prune;
     int32_t fault_band;      // testing: this band never publishes (-1 = off)
@@ -43,6 +45,10 @@ struct FwdParams {
 
 // rows per thread supported by the forward kernel
 bool fwd_rpt_supported(int rpt);
+// int16x2 forward kernel (local mode, alphabet <= 4): 64*rpt rows per band
+bool fwd16_rpt_supported(int rpt);
+cudaError_t fwd16_launch(const FwdParams &p, int rpt, int ctas, cudaStream_t s);
+cudaError_t fwd16_occupancy(int rpt, int *ctas_per_sm);
 cudaError_t fwd_launch(const FwdParams &p, int rpt, bool two_word_profile, int ctas,
                        int threads, cudaStream_t s);
 cudaError_t fwd_occupancy(int rpt, bool two_word_profile, int threads, int *ctas_per_sm);

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(128) lab_kernel(const LabParams P)
         const bool fresh = ck > 0 && band > 0 && (band % ck) == 0;
         const bool ckpt_band = ck > 0 && ((band + 1) % ck) == 0 && band + 1 < pr.nbands;
         int4 *ck_row = ckpt_band ? pr.ckpt + (size_t)((band + 1) / ck - 1) * (size_t)m : nullptr;
-        const bool src_f = pr.src == ST_F, src_e = pr.src == ST_E;
+        const bool src_f = pr.src == ST_F;
         const int blab = (ck > 0 && band >= ck) ? ((0 << 2) | (go == ge ? LAB_OPEN : LAB_EXT)) : LAB_INIT;
         const int prev_blab = (ck > 0 && band - 1 >= ck) ? ((0 << 2) | (go == ge ? LAB_OPEN : LAB_EXT)) : LAB_INIT;
 

@@ -82,6 +82,23 @@ cudaError_t reverse_copy_launch(const uint8_t *src, uint8_t *dst, int64_t len, c
     return cudaGetLastError();
 }
 
+// one block per segment: dst[dst_off + i] = src[src_off + len - 1 - i]
+__global__ void reverse_segments_kernel(const uint8_t *src, uint8_t *dst, const int64_t *src_off,
+                                        const int64_t *dst_off, const int32_t *len)
+{
+    const int k = blockIdx.x;
+    const int64_t so = src_off[k], d0 = dst_off[k];
+    const int L = len[k];
+    for (int i = threadIdx.x; i < L; i += blockDim.x) dst[d0 + i] = src[so + L - 1 - i];
+}
+cudaError_t reverse_segments_launch(const uint8_t *src, uint8_t *dst, const int64_t *src_off,
+                                    const int64_t *dst_off, const int32_t *len, int count, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    reverse_segments_kernel<<<count, 256, 0, s>>>(src, dst, src_off, dst_off, len);
+    return cudaGetLastError();
+}
+
 __global__ void fill_i32_kernel(int32_t *p, int32_t v, int64_t count)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;

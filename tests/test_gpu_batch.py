@@ -1,0 +1,154 @@
+"""Parity of the batched path (sw_align_batch) with the CPU oracle.
+
+Pairs of very different lengths share one persistent launch; pairs are
+transposed when B is longer, run on int16x2 lanes when their score bound fits,
+and re-run on int32 lanes after an int16 overflow.  Every pair must match the
+oracle bit for bit (score, end point; start point and CIGAR when aligned), and
+the batch must match the single-pair entry points.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from gen import synth
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def sw():
+    import paper_1304_5966_gb300 as m
+    from paper_1304_5966_gb300 import build
+    build.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(sw):
+    c = sw.sw_ctx_create(0, workspace_bytes=4 << 30)
+    yield c
+    c.close()
+
+
+def _mixed_pairs(count, seed, lo=1, hi=3000):
+    st = synth.Rng(seed).stream()
+    pairs = []
+    for t in range(count):
+        n = int(synth.log_uniform_int(st, lo, hi, 1)[0])
+        m = int(synth.log_uniform_int(st, lo, hi, 1)[0])
+        if t % 3 == 0:
+            a, b = synth.random_pair(n, m, seed=seed * 1000 + t)
+        else:
+            a, b0 = synth.related_pair(max(n, m), seed=seed * 1000 + t)
+            a, b = a[:n], b0[:m]
+        pairs.append((a, b))
+    pairs.append((np.zeros(0, np.uint8), np.zeros(7, np.uint8)))     # empty side
+    pairs.append((np.array([2], np.uint8), np.array([2], np.uint8)))  # 1 x 1
+    return pairs
+
+
+def _se(r):
+    return (r.score, r.a_end, r.b_end) if r.score else (0, -1, -1)
+
+
+def test_score_only_mixed(sw, ctx):
+    pairs = _mixed_pairs(150, 1)
+    got = sw.sw_align_batch(ctx, pairs, flags=sw.SW_FLAG_SCORE_ONLY)
+    for (a, b), r in zip(pairs, got):
+        S, ei, ej = oracle.local_score(a, b)
+        assert _se(r) == ((S, ei, ej) if S else (0, -1, -1)), (len(a), len(b))
+
+
+@pytest.mark.parametrize("flags", ["FORCE_INT32", "NO_PRUNE"])
+def test_score_only_variants_identical(sw, ctx, flags):
+    pairs = _mixed_pairs(80, 2)
+    base = sw.sw_align_batch(ctx, pairs, flags=sw.SW_FLAG_SCORE_ONLY)
+    other = sw.sw_align_batch(ctx, pairs, flags=sw.SW_FLAG_SCORE_ONLY | getattr(sw, "SW_FLAG_" + flags))
+    assert [_se(r) for r in base] == [_se(r) for r in other]
+
+
+def test_int16_overflow_rerun(sw, ctx):
+    # match 100: bound 100 * min(n, m) exceeds int16 for the longer pairs; forcing
+    # int16 lanes must detect it and re-run those pairs on int32 lanes
+    sch = oracle.Scheme(100, -90, 120, 40)
+    s = sw.Scheme(100, -90, 120, 40)
+    pairs = _mixed_pairs(40, 3, lo=100, hi=1500)
+    got = sw.sw_align_batch(ctx, pairs, s, flags=sw.SW_FLAG_SCORE_ONLY | sw.SW_FLAG_FORCE_INT16)
+    assert got[0].stats["int16_reruns"] > 0
+    for (a, b), r in zip(pairs, got):
+        S, ei, ej = oracle.local_score(a, b, sch)
+        assert _se(r) == ((S, ei, ej) if S else (0, -1, -1))
+
+
+def test_align_mixed(sw, ctx):
+    pairs = _mixed_pairs(40, 4, lo=1, hi=1500)
+    got = sw.sw_align_batch(ctx, pairs)
+    for (a, b), r in zip(pairs, got):
+        w = oracle.align(a, b)
+        assert (r.score, r.a_begin, r.a_end, r.b_begin, r.b_end, r.cigar or "") == \
+            (w.score, w.a_begin, w.a_end, w.b_begin, w.b_end, w.cigar), (len(a), len(b))
+
+
+def test_batch_equals_single(sw, ctx):
+    pairs = _mixed_pairs(12, 5, lo=200, hi=2500)
+    got = sw.sw_align_batch(ctx, pairs)
+    for (a, b), r in zip(pairs, got):
+        one = sw.sw_align(ctx, a, b)
+        assert (r.score, r.a_begin, r.a_end, r.b_begin, r.b_end, r.cigar) == \
+            (one.score, one.a_begin, one.a_end, one.b_begin, one.b_end, one.cigar)
+
+
+def test_asymmetric_matrix(sw, ctx):
+    # s(x, y) != s(y, x): transposed problems must use the transposed table
+    mat = (2, -1, -3, 0,
+           -2, 3, -1, -4,
+           0, -3, 1, -2,
+           -1, -2, -4, 2)
+    sch = oracle.Scheme(alphabet=4, matrix=mat)
+    s = sw.Scheme(alphabet=4, matrix=mat)
+    pairs = _mixed_pairs(30, 6, lo=50, hi=1200)
+    got = sw.sw_align_batch(ctx, pairs, s, flags=sw.SW_FLAG_SCORE_ONLY)
+    for (a, b), r in zip(pairs, got):
+        S, ei, ej = oracle.local_score(a, b, sch)
+        assert _se(r) == ((S, ei, ej) if S else (0, -1, -1))
+    for (a, b) in pairs[:8]:
+        w = oracle.align(a, b, sch)
+        r = sw.sw_align(ctx, a, b, s)
+        assert (r.score, r.a_begin, r.a_end, r.b_begin, r.b_end, r.cigar or "") == \
+            (w.score, w.a_begin, w.a_end, w.b_begin, w.b_end, w.cigar)
+    # a wide pair (B much longer) forces transposed label passes
+    a, b = synth.related_pair(2500, seed=61)
+    a = a[700:1500]
+    w = oracle.align(a, b, sch)
+    ctx.set_option(sw.SW_OPT_CKPT_BANDS, 1)
+    ctx.set_option(sw.SW_OPT_LEAF_CELLS, 256)
+    try:
+        r = sw.sw_align(ctx, a, b, s)
+    finally:
+        ctx.set_option(sw.SW_OPT_CKPT_BANDS, 0)
+        ctx.set_option(sw.SW_OPT_LEAF_CELLS, 1 << 16)
+    assert (r.score, r.a_begin, r.a_end, r.b_begin, r.b_end, r.cigar or "") == \
+        (w.score, w.a_begin, w.a_end, w.b_begin, w.b_end, w.cigar)
+
+
+def test_device_inputs(sw, ctx):
+    import torch
+    pairs = _mixed_pairs(20, 7, lo=10, hi=2000)
+    dev = [(torch.from_numpy(a.copy()).cuda(), torch.from_numpy(b.copy()).cuda()) for a, b in pairs]
+    got = sw.sw_align_batch(ctx, dev)
+    for (a, b), r in zip(pairs, got):
+        w = oracle.align(a, b)
+        assert (r.score, r.a_begin, r.a_end, r.b_begin, r.b_end, r.cigar or "") == \
+            (w.score, w.a_begin, w.a_end, w.b_begin, w.b_end, w.cigar)
+
+
+def test_batch_4096_golden(sw, ctx):
+    g = json.load(open(os.path.join(HERE, "golden", "batch_4096.json")))
+    pairs = synth.batch_pairs()
+    got = sw.sw_align_batch(ctx, pairs, flags=sw.SW_FLAG_SCORE_ONLY)
+    want = [tuple(x) if x[0] else (0, -1, -1) for x in g["score_end"]]
+    assert [_se(r) for r in got] == want
