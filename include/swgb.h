@@ -168,6 +168,31 @@ int sw_score_plain(sw_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, i
 
 void sw_result_free(sw_result *r);
 
+/* Score and end point, like sw_score, for callers that cannot allocate device
+ * memory at call time: processes whose device memory is all reserved up front by
+ * their framework's caching allocator, or latency-bound pipelines that forbid
+ * cudaMalloc/cudaFree (and the synchronisation they imply) on the hot path.  The
+ * paper has no counterpart; this is a deployment variant of the forward pass.
+ *
+ * a[0..n) and b[0..m) are codes in DEVICE memory; `stream` is the cudaStream_t to
+ * run on (NULL = legacy default stream) and the call returns after synchronising
+ * it; `out` is host memory (score, a_end, b_end and stats; no CIGAR).  No device
+ * memory is allocated or freed and no context is needed: the scratch (boundary
+ * row, flags, band records, counters) is one library-wide static device array of
+ * 10 MiB that every GPU loading the library keeps until the process exits.
+ * Limits: n <= 16,777,216 and m <= 1,048,576; larger inputs return SW_ENOMEM
+ * (the static scratch cannot hold them; use sw_score).  Codes >= alphabet return
+ * SW_EINVAL, an expired inter-band wait SW_ETIMEOUT.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array, which keeps the previous call's
+ * contents (each call re-initialises what it needs): calls that overlap on the
+ * GPU -- from several host threads or streams at once -- race and give wrong
+ * results, so serialise them. */
+int sw_score_static(const uint8_t *a, int64_t n, const uint8_t *b, int64_t m,
+                    const sw_scheme *scheme, void *stream, sw_result *out);
+
 /* Diagnostics: measured issue rate on `device`, per SM clock, with independent
  * chains at full occupancy.  Kinds 0-5, 7, 8, 10 give lane operations per clock
  * per SM of one instruction: 0 IADD+LOP pair, 1 IMNMX+IADD pair, 2 DPX

@@ -90,6 +90,7 @@ def lib():
                                        ctypes.POINTER(_Result)]
         L.sw_align_batch.argtypes = [P, ctypes.POINTER(_Pair), i32, ctypes.POINTER(_Scheme), i32,
                                      ctypes.POINTER(_Result)]
+        L.sw_score_static.argtypes = [P, i64, P, i64, ctypes.POINTER(_Scheme), P, ctypes.POINTER(_Result)]
         L.sw_result_free.argtypes = [ctypes.POINTER(_Result)]
         L.sw_result_free.restype = None
         _lib = L
@@ -255,3 +256,21 @@ def sw_align_batch(ctx: Context, pairs, scheme: Scheme | None = None, flags: int
     for k in range(len(pairs)):
         lib().sw_result_free(ctypes.byref(outs[k]))
     return res
+
+
+def sw_score_static(a, b, scheme: Scheme | None = None, stream=None) -> Result:
+    """Score and end point without any device allocation (library-wide static
+    scratch; device inputs only; n <= 16,777,216, m <= 1,048,576).  For callers
+    that cannot allocate device memory at call time.  Calls must not overlap."""
+    import torch
+    pa, n, da, ka = _seq(a)
+    pb, m, db, kb = _seq(b)
+    if not (da and db):
+        raise ValueError("sw_score_static takes device sequences")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    sch, keep = (scheme or DNA)._c()
+    res = _Result()
+    st = lib().sw_score_static(pa, n, pb, m, ctypes.byref(sch), ctypes.c_void_p(s.cuda_stream), ctypes.byref(res))
+    if st != SW_OK:
+        raise SwError(st, f"sw_score_static: {lib().sw_strerror(st).decode()}")
+    return _result(res)
