@@ -168,6 +168,32 @@ int sw_score_plain(sw_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, i
 
 void sw_result_free(sw_result *r);
 
+/* ---- Serving: continuous batching of requests -------------------------------
+ * A server owns `workers` worker threads, each with its own CUDA stream and a
+ * slice of `ctx`'s workspace (device_budget bytes in total, 0 = all that is
+ * free; the slices stay reserved until sw_server_destroy).  Requests are host
+ * sequences, copied at submit.  A free worker takes every queued request that
+ * fits its slice (same scheme, first come first served) and runs them as one
+ * batch; requests arriving meanwhile go to the next free worker, whose kernels
+ * overlap the running ones on the device.  Each result is identical to the
+ * same request run alone.  flags: SW_FLAG_SCORE_ONLY (else full alignment),
+ * SW_FLAG_NO_PRUNE.  `ctx` must outlive the server and not be used for other
+ * calls while the server exists. */
+typedef struct sw_server sw_server;
+int sw_server_create(sw_ctx *ctx, int32_t workers, uint64_t device_budget, sw_server **out);
+/* SW_EBUSY: refused by admission (the request's device footprint exceeds a
+ * worker's slice, or the queued footprint would exceed four times the budget). */
+int sw_server_submit(sw_server *srv, const uint8_t *a, int64_t n, const uint8_t *b, int64_t m,
+                     const sw_scheme *scheme, int32_t flags, uint64_t *ticket);
+/* Waits up to timeout_us (-1: forever) for the result.  SW_EPENDING if not done
+ * (the ticket stays valid); otherwise the request's status, `out` filled (the
+ * caller owns out->cigar: sw_result_free) and the ticket retired. */
+int sw_server_poll(sw_server *srv, uint64_t ticket, sw_result *out, int64_t timeout_us);
+/* Removes a request that has not started (SW_OK); SW_EBUSY once it is running. */
+int sw_server_cancel(sw_server *srv, uint64_t ticket);
+/* Finishes the queued work, then releases the workers and their slices. */
+void sw_server_destroy(sw_server *srv);
+
 /* Score and end point, like sw_score, for callers that cannot allocate device
  * memory at call time: processes whose device memory is all reserved up front by
  * their framework's caching allocator, or latency-bound pipelines that forbid

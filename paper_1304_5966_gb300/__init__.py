@@ -91,6 +91,13 @@ def lib():
         L.sw_align_batch.argtypes = [P, ctypes.POINTER(_Pair), i32, ctypes.POINTER(_Scheme), i32,
                                      ctypes.POINTER(_Result)]
         L.sw_score_static.argtypes = [P, i64, P, i64, ctypes.POINTER(_Scheme), P, ctypes.POINTER(_Result)]
+        L.sw_server_create.argtypes = [P, i32, ctypes.c_uint64, ctypes.POINTER(P)]
+        L.sw_server_submit.argtypes = [P, P, i64, P, i64, ctypes.POINTER(_Scheme), i32,
+                                       ctypes.POINTER(ctypes.c_uint64)]
+        L.sw_server_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(_Result), i64]
+        L.sw_server_cancel.argtypes = [P, ctypes.c_uint64]
+        L.sw_server_destroy.argtypes = [P]
+        L.sw_server_destroy.restype = None
         L.sw_result_free.argtypes = [ctypes.POINTER(_Result)]
         L.sw_result_free.restype = None
         _lib = L
@@ -274,3 +281,59 @@ def sw_score_static(a, b, scheme: Scheme | None = None, stream=None) -> Result:
     if st != SW_OK:
         raise SwError(st, f"sw_score_static: {lib().sw_strerror(st).decode()}")
     return _result(res)
+
+
+class Server:
+    """Continuous-batching request server (sw_server_*).  submit() copies the
+    host sequences and returns a ticket; poll() waits for the result."""
+
+    def __init__(self, ctx: Context, workers: int = 4, device_budget: int = 0):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        st = lib().sw_server_create(ctx.handle, workers, device_budget, ctypes.byref(h))
+        if st != SW_OK:
+            raise SwError(st, "sw_server_create failed")
+        self.handle = h
+
+    def submit(self, a, b, scheme: Scheme | None = None, score_only: bool = False, flags: int = 0) -> int:
+        pa, n, da, ka = _seq(a)
+        pb, m, db, kb = _seq(b)
+        if da or db:
+            raise ValueError("server requests take host sequences")
+        sch, keep = (scheme or DNA)._c()
+        t = ctypes.c_uint64()
+        st = lib().sw_server_submit(self.handle, pa, n, pb, m, ctypes.byref(sch),
+                                    flags | (SW_FLAG_SCORE_ONLY if score_only else 0), ctypes.byref(t))
+        if st != SW_OK:
+            raise SwError(st, f"sw_server_submit: {lib().sw_strerror(st).decode()}")
+        return int(t.value)
+
+    def poll(self, ticket: int, timeout_us: int = -1):
+        """The Result, or None while the request is pending."""
+        res = _Result()
+        st = lib().sw_server_poll(self.handle, ticket, ctypes.byref(res), timeout_us)
+        if st == SW_EPENDING:
+            return None
+        out = _result(res)
+        lib().sw_result_free(ctypes.byref(res))
+        if st != SW_OK:
+            raise SwError(st, f"request {ticket}: {lib().sw_strerror(st).decode()}")
+        return out
+
+    def cancel(self, ticket: int) -> int:
+        return lib().sw_server_cancel(self.handle, ticket)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sw_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sw_server_create(ctx: Context, workers: int = 4, device_budget: int = 0) -> Server:
+    return Server(ctx, workers, device_budget)
