@@ -162,6 +162,91 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_batch(sw, ctx, reps: int = 3):
+    """4,096 pairs (lengths log-uniform 100..20,000 per side): one batched call vs
+    the single-pair path (sw_score per pair) and the plain anti-diagonal path."""
+    import torch
+    from gen import synth
+    pairs = synth.batch_pairs()
+    cells = sum(len(a) * len(b) for a, b in pairs)
+    sw.sw_align_batch(ctx, pairs, flags=sw.SW_FLAG_SCORE_ONLY)          # warm-up
+    ts, st = [], None
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = sw.sw_align_batch(ctx, pairs, flags=sw.SW_FLAG_SCORE_ONLY)
+        ts.append(time.perf_counter() - t0)
+        st = res[0].stats
+    batch_s = min(ts)
+    # single-pair path and plain path on a seeded sample of the same pairs
+    sample = pairs[::16]
+    scells = sum(len(a) * len(b) for a, b in sample)
+    t0 = time.perf_counter()
+    for a, b in sample:
+        sw.sw_score(ctx, a, b)
+    single_s = time.perf_counter() - t0
+    psample = pairs[::256]
+    pcells = sum(len(a) * len(b) for a, b in psample)
+    t0 = time.perf_counter()
+    for a, b in psample:
+        sw.sw_score_plain(ctx, a, b)
+    plain_s = time.perf_counter() - t0
+    g = cells / batch_s / 1e9
+    return {"pairs": len(pairs), "cells": cells, "ms": round(batch_s * 1e3, 2), "gcups": round(g, 1),
+            "kernel_ms": round(st["ms_forward"], 2), "int16_reruns": st["int16_reruns"],
+            "single_pair_path_gcups": round(scells / single_s / 1e9, 1),
+            "plain_path_gcups": round(pcells / plain_s / 1e9, 2),
+            "vs_single_pair_path": round(g / (scells / single_s / 1e9), 2),
+            "vs_plain_path": round(g / (pcells / plain_s / 1e9), 1),
+            "note": "wall time of the score-only batch call incl. H2D of the packed pairs; "
+                    "single-pair path timed on every 16th pair, plain path on every 256th"}
+
+
+def bench_serving(sw, ctx, rates=(10.0, 100.0), count: int = 40):
+    """Poisson arrivals of pairs with L log-uniform in [1e3, 1e6] (70 % score-only,
+    30 % alignment), submitted at their arrival times to a 4-worker server."""
+    import threading
+    from gen import synth
+    out = []
+    for rate in rates:
+        stream = synth.serve_stream(count, rate, seed=5)
+        srv = sw.Server(ctx, workers=4, device_budget=16 << 30)
+        sub, done = {}, {}
+        tickets = [None] * count
+        t_start = time.perf_counter()
+
+        def producer():
+            for k, (t_arr, a, b, align) in enumerate(stream):
+                dt = t_start + t_arr - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                sub[k] = time.perf_counter()
+                tickets[k] = srv.submit(a, b, score_only=not align)
+
+        th = threading.Thread(target=producer)
+        th.start()
+        pending = set(range(count))
+        while pending:
+            for k in list(pending):
+                if tickets[k] is None:
+                    continue
+                r = srv.poll(tickets[k], timeout_us=0)
+                if r is not None:
+                    done[k] = time.perf_counter()
+                    pending.discard(k)
+            time.sleep(0.0005)
+        th.join()
+        srv.close()
+        lat = sorted(done[k] - sub[k] for k in range(count))
+        span = max(done.values()) - min(sub.values())
+        cells = sum(len(a) * len(b) for _, a, b, _ in stream)
+        out.append({"offered_rps": rate, "requests": count,
+                    "p50_ms": round(1e3 * lat[len(lat) // 2], 1),
+                    "p99_ms": round(1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))], 1),
+                    "achieved_rps": round(count / span, 2), "sustained_gcups": round(cells / span / 1e9, 1)})
+    return out
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -260,6 +345,10 @@ def main():
                                 "ours_gcups_same_sample": round(ps * ps / rq.stats["ms_forward"] / 1e6, 1),
                                 "vs_plain_full_step": round((n * m / (total / args.steps) / 1e9) /
                                                             (ps * ps / rp.stats["ms_forward"] / 1e6), 1)}
+
+    if not args.no_extras and rank == 0:
+        extras["batch"] = bench_batch(sw, ctx)
+        extras["serving"] = bench_serving(sw, ctx)
 
     if rank != 0:
         return
