@@ -127,14 +127,19 @@ const char *sw_strerror(int status);
  *                           progress (-1 = off), so the next band's bounded wait
  *                           expires and the call returns SW_ETIMEOUT
  *   SW_OPT_CKPT_BANDS       reconstruction: bands between checkpoint rows at level 0
- *   SW_OPT_LEAF_CELLS       reconstruction: largest sub-problem solved by full traceback */
+ *   SW_OPT_LEAF_CELLS       reconstruction: largest sub-problem solved by full traceback
+ *   SW_OPT_FORWARD_LANES    single-pair forward and start passes: 0 = int16x2 lanes
+ *                           with per-warp offsets when the scheme allows, else int32;
+ *                           16 = always try int16x2; 32 = int32 lanes only.  The
+ *                           result is identical either way. */
 enum {
     SW_OPT_ROWS_PER_THREAD = 1,
     SW_OPT_WARPS_PER_SM = 2,
     SW_OPT_TIMEOUT_MS = 3,
     SW_OPT_FAULT_BAND = 4,
     SW_OPT_CKPT_BANDS = 5,
-    SW_OPT_LEAF_CELLS = 6
+    SW_OPT_LEAF_CELLS = 6,
+    SW_OPT_FORWARD_LANES = 7
 };
 int sw_ctx_set_option(sw_ctx *ctx, int option, int64_t value);
 

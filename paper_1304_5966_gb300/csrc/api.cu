@@ -91,12 +91,24 @@ static int auto_rpt(sw_ctx *ctx, const std::vector<FwdJob> &jobs, bool p2)
     return 8;
 }
 
-static int auto_rpt16(sw_ctx *ctx, const std::vector<FwdJob> &jobs)
+// int16x2 lanes with per-warp offsets: all true values of a band's window
+// (64*rpt rows x 96 columns) lie within (64*rpt + 96)(go + max_sub) of each other;
+// they must stay between the offset's sentinel floor and the top of int16.
+static bool rel16_fits(const SchemeDev &sc, int rpt)
+{
+    if (sc.alphabet > 4) return false;
+    if (sc.go + sc.ge - sc.min_sub > 255 || sc.max_sub > 127) return false;
+    const int64_t spread = (int64_t)(64 * rpt + 96) * (sc.go + sc.max_sub) + 64 * sc.max_sub;
+    return spread <= 44000;
+}
+
+static int auto_rpt16(sw_ctx *ctx, const std::vector<FwdJob> &jobs, bool rel, const SchemeDev &sc)
 {
     const int cands[3] = {16, 8, 4};
     for (int k = 0; k < 3; ++k) {
+        if (rel && !rel16_fits(sc, cands[k])) continue;
         int per_sm = 1;
-        if (fwd16_occupancy(cands[k], &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+        if (fwd16_occupancy(cands[k], rel, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
         const double warps = 4.0 * per_sm * ctx->sms;
         int64_t bands = 0, rows = 0;
         for (auto &j : jobs) { bands += (j.n + 64 * cands[k] - 1) / (64 * cands[k]); rows += j.n; }
@@ -107,14 +119,14 @@ static int auto_rpt16(sw_ctx *ctx, const std::vector<FwdJob> &jobs)
 }
 
 static int run_forward_impl(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &jobs, bool prune,
-                            int rpt, bool lane16, std::vector<int4> &res, std::vector<int> *ovf,
+                            int rpt, bool lane16, bool rel, std::vector<int4> &res, std::vector<int> *ovf,
                             sw_stats *stats, float *ms)
 {
     const int np = (int)jobs.size();
     res.assign(np, make_int4(0, 0, 0, 0));
     if (ovf) ovf->assign(np, 0);
     if (np == 0) return SW_OK;
-    if (rpt <= 0) rpt = lane16 ? auto_rpt16(ctx, jobs) : auto_rpt(ctx, jobs, sc.alphabet > 4);
+    if (rpt <= 0) rpt = lane16 ? auto_rpt16(ctx, jobs, rel, sc) : auto_rpt(ctx, jobs, sc.alphabet > 4);
     const int R = (lane16 ? 64 : 32) * rpt;
     Scope sc_(ctx->arena);
     std::vector<FwdProblem> hp(np);
@@ -196,7 +208,7 @@ static int run_forward_impl(sw_ctx *ctx, const SchemeDev &sc, const std::vector<
     int ctas;
     if (lane16) {
         int per_sm = 1;
-        if (fwd16_occupancy(rpt, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+        if (fwd16_occupancy(rpt, rel, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
         if (ctx->opt.warps_per_sm > 0) per_sm = std::max(1, std::min(per_sm, ctx->opt.warps_per_sm / 4));
         ctas = per_sm * ctx->sms;
     } else {
@@ -204,7 +216,7 @@ static int run_forward_impl(sw_ctx *ctx, const SchemeDev &sc, const std::vector<
     }
     ctas = (int)std::min<int64_t>(ctas, (ntk + 3) / 4);
     cudaEventRecord(ctx->ev[0], s);
-    if ((e = lane16 ? fwd16_launch(P, rpt, ctas, s) : fwd_launch(P, rpt, p2, ctas, 128, s)))
+    if ((e = lane16 ? fwd16_launch(P, rpt, rel, ctas, s) : fwd_launch(P, rpt, p2, ctas, 128, s)))
         return set_cuda_error(ctx, e, "forward launch");
     cudaEventRecord(ctx->ev[1], s);
     if ((e = fwd_reduce_launch(dprobs, np, dres, s))) return set_cuda_error(ctx, e, "forward reduce");
@@ -236,16 +248,43 @@ static int run_forward_impl(sw_ctx *ctx, const SchemeDev &sc, const std::vector<
     return SW_OK;
 }
 
+int run_forward32(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &jobs, bool prune,
+                  int rpt, std::vector<int4> &res, sw_stats *stats, float *ms)
+{
+    return run_forward_impl(ctx, sc, jobs, prune, rpt, false, false, res, nullptr, stats, ms);
+}
+
+// Forward pass of long problems: int16x2 lanes with per-warp offsets when the
+// scheme's value spread allows (and the context does not force int32 lanes),
+// int32 lanes otherwise or for any problem whose offset could not absorb a jump.
 int run_forward(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &jobs, bool prune,
                 int rpt, std::vector<int4> &res, sw_stats *stats, float *ms)
 {
-    return run_forward_impl(ctx, sc, jobs, prune, rpt, false, res, nullptr, stats, ms);
+    const bool rel_ok = ctx->opt.forward_lanes != 32 && rel16_fits(sc, 4) &&
+                        (ctx->opt.forward_lanes == 16 || rpt <= 0);
+    if (!rel_ok) return run_forward32(ctx, sc, jobs, prune, rpt, res, stats, ms);
+    std::vector<int> ovf;
+    const int rpt16 = (ctx->opt.forward_lanes == 16 && fwd16_rpt_supported(rpt) && rel16_fits(sc, rpt)) ? rpt : 0;
+    int st = run_forward_impl(ctx, sc, jobs, prune, rpt16, true, true, res, &ovf, stats, ms);
+    if (st) return st;
+    std::vector<FwdJob> redo;
+    std::vector<int> idx;
+    for (size_t p = 0; p < jobs.size(); ++p)
+        if (ovf[p]) { redo.push_back(jobs[p]); idx.push_back((int)p); }
+    if (redo.empty()) return SW_OK;
+    if (stats) stats->int16_reruns += (int32_t)redo.size();
+    std::vector<int4> r2;
+    float ms2 = 0;
+    if ((st = run_forward32(ctx, sc, redo, prune, fwd_rpt_supported(rpt) ? rpt : 0, r2, stats, &ms2))) return st;
+    for (size_t k = 0; k < idx.size(); ++k) res[idx[k]] = r2[k];
+    if (ms) *ms += ms2;
+    return SW_OK;
 }
 
 int run_forward16(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &jobs, bool prune,
                   int rpt, std::vector<int4> &res, std::vector<int> &ovf, sw_stats *stats, float *ms)
 {
-    return run_forward_impl(ctx, sc, jobs, prune, rpt, true, res, &ovf, stats, ms);
+    return run_forward_impl(ctx, sc, jobs, prune, rpt, true, false, res, &ovf, stats, ms);
 }
 
 // copy (or borrow) a sequence to the device and check its codes
@@ -360,7 +399,7 @@ int sw_ctx_set_option(sw_ctx *ctx, int option, int64_t value)
     if (!ctx) return SW_EINVAL;
     switch (option) {
     case SW_OPT_ROWS_PER_THREAD:
-        if (value != 0 && !fwd_rpt_supported((int)value)) return SW_EINVAL;
+        if (value != 0 && !fwd_rpt_supported((int)value) && !fwd16_rpt_supported((int)value)) return SW_EINVAL;
         ctx->opt.rows_per_thread = (int)value; return SW_OK;
     case SW_OPT_WARPS_PER_SM:
         if (value < 0 || value > 64) return SW_EINVAL;
@@ -374,6 +413,9 @@ int sw_ctx_set_option(sw_ctx *ctx, int option, int64_t value)
     case SW_OPT_CKPT_BANDS:
         if (value < 0 || value > 1000000) return SW_EINVAL;
         ctx->opt.ckpt_bands = (int)value; return SW_OK;
+    case SW_OPT_FORWARD_LANES:
+        if (value != 0 && value != 16 && value != 32) return SW_EINVAL;
+        ctx->opt.forward_lanes = (int)value; return SW_OK;
     case SW_OPT_LEAF_CELLS:
         if (value < 256 || value > (1 << 18)) return SW_EINVAL;
         ctx->opt.leaf_cells = value; return SW_OK;

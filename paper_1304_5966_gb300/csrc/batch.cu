@@ -78,7 +78,7 @@ int batch_forward(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const uin
     }
     if (!j32.empty()) {
         std::vector<int4> res;
-        if ((st = run_forward(ctx, sc, j32, prune, 0, res, stats, &ms2))) return st;
+        if ((st = run_forward32(ctx, sc, j32, prune, 0, res, stats, &ms2))) return st;
         for (size_t k = 0; k < j32.size(); ++k) store(id32[k], res[k]);
     }
     if (ms_total) *ms_total = ms + ms2;

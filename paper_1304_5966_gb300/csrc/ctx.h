@@ -108,6 +108,7 @@ struct Options {
     int fault_band = -1;
     int ckpt_bands = 0;            // 0 = choose from the workspace size
     int64_t leaf_cells = 1 << 16;
+    int forward_lanes = 0;         // 0 auto, 16 int16x2 (offset) lanes, 32 int32 lanes
 };
 
 }  // namespace swgb
@@ -144,5 +145,7 @@ struct FwdJob {
 };
 int run_forward(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &jobs, bool prune,
                 int rpt, std::vector<int4> &res, sw_stats *stats, float *ms);
+int run_forward32(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &jobs, bool prune,
+                  int rpt, std::vector<int4> &res, sw_stats *stats, float *ms);
 
 }  // namespace swgb

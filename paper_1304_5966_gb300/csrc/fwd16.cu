@@ -1,23 +1,35 @@
-// fwd16.cu -- forward local pass on int16x2 lanes (sm_103a DPX 16x2 forms).
+// fwd16.cu -- forward pass on int16x2 lanes (sm_103a DPX 16x2 forms).
 //
-// Same computation and tie rule as fwd.cu (FWD_LOCAL), with two cells per
-// register: a warp owns a band of 64*RPT rows, lane t holds the rows of
-// "virtual lane" t in the low halfword and of virtual lane t+32 in the high
-// halfword of every state register.  Virtual lane v processes column j at step
-// j + v, so the high half runs 32 columns behind the low half.  Each step the
-// bottom row of every virtual lane moves to the next one by a rotating shuffle
-// (lane 0's high half receives lane 31's low half); lane 0's low half reads the
-// row above the band from the shared-memory chunk, lane 31's high half writes
-// the band's bottom row.  Scores are absolute int16: the host routes a pair here
-// only when max_sub * min(n, m) and the gap costs stay inside int16, and a value
-// reaching the guard (32767 - max_sub) sets the problem's overflow word so the
-// pair is re-run on int32 lanes (the first value to reach the guard is computed
-// before anything can wrap, since H grows by at most max_sub per step).
+// Same computation and tie rule as fwd.cu, with two cells per register: a warp
+// owns a band of 64*RPT rows, lane t holds the rows of "virtual lane" t in the
+// low halfword and of virtual lane t+32 in the high halfword of every state
+// register.  Virtual lane v processes column j at step j + v, so the high half
+// runs 32 columns behind the low half.  Each step the bottom row of every
+// virtual lane moves to the next one by a rotating shuffle (lane 0's high half
+// receives lane 31's low half); lane 0's low half reads the row above the band
+// from the shared-memory chunk, lane 31's high half writes the band's bottom row.
+//
+// Two value encodings (template REL):
+//  * absolute (REL = false, local mode, batches): int16 scores; the host routes
+//    a pair here only when its score bound fits, and a value reaching the guard
+//    (32767 - max_sub) sets the problem's overflow word so the pair is re-run on
+//    int32 lanes (the first value reaching the guard is computed before anything
+//    can wrap, since H grows by at most max_sub per step).
+//  * relative (REL = true, local and anchored modes, single long pairs): every
+//    value is stored minus a warp-wide offset O, re-chosen at each 32-step block
+//    so the largest live value sits at 16384.  Horizontally or vertically
+//    adjacent cells differ by at most go + max_sub, so all true values of a
+//    band's window (64*RPT rows x 96 columns) lie within (64*RPT + 96) *
+//    (go + max_sub) of each other; the host uses this encoding only when that
+//    spread fits.  Minus infinity (anchored borders) and skipped cells are the
+//    sentinel FLOOR = -32512, which lies below every true value of the window
+//    and above anything an add can wrap from.  The local zero floor is the
+//    register fl2 = max(-O, FLOOR).  The boundary row in HBM stays absolute
+//    int32 (converted when a chunk enters shared memory / leaves lane 31).
 //
 // Per cell pair: prmt (both substitution scores), viaddmax16x2 (F),
-// viaddmax16x2 (diag + s vs E), vimax3_16x2 (with F and the zero floor),
-// viaddmax16x2 (H - go), viaddmax16x2 (E), and half a vimax3_16x2 for the
-// running maximum.
+// viaddmax16x2 (diag + s vs E), vimax3_16x2 (with F and the floor),
+// viaddmax16x2 (H - go), viaddmax16x2 (E), vimax16x2 for the running maximum.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -37,7 +49,22 @@ __device__ __forceinline__ uint32_t perm(uint32_t a, uint32_t b, uint32_t s) {
 // the high half's selector is the same plus 0x44 (bytes 4-7)
 __device__ __forceinline__ uint32_t sel_lo8(uint32_t c) { return c | ((c | 8u) << 4); }
 
-template <int RPT>
+// per-halfword max of two (DPX three-input form with a repeated operand)
+__device__ __forceinline__ uint32_t vmax16(uint32_t a, uint32_t b) { return __vimax3_s16x2(a, b, b); }
+
+constexpr int REL_FLOOR = -32768 + 256;
+constexpr int REL_TOP = 16384;
+
+// absolute int32 -> relative int16 range; anchored minus infinity (biased values
+// below BIAS/2) and anything below the window become FLOOR
+__device__ __forceinline__ int to_rel(int v, int O, bool anch)
+{
+    if (anch && v < BIAS / 2) return REL_FLOOR;
+    const long long r = (long long)v - O;
+    return (int)(r < REL_FLOOR ? REL_FLOOR : (r > 32767 ? 32767 : r));
+}
+
+template <int RPT, bool REL>
 __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
 {
     __shared__ int4 s_in_all[4][3][CH];   // {H, F, selector8, 0} per column, three chunks
@@ -48,7 +75,8 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
     int2 *s_out = s_out_all[wid];
     const int go = P.go, ge = P.ge;
     const uint32_t go2 = p16(-go, -go), ge2 = p16(-ge, -ge);
-    const uint32_t NEG2 = p16(-32768, -32768), ZERO2 = 0u;
+    const uint32_t NEG2 = REL ? p16(REL_FLOOR, REL_FLOOR) : p16(-32768, -32768);
+    const uint32_t ZERO2 = 0u;
     const int src_lane = (lane + 31) & 31;
     constexpr int R = 64 * RPT;
 
@@ -63,11 +91,16 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
         const int band = tb.y;
         const int n = pr.n, m = pr.m;
         const bool transposed = pr.transposed != 0;
+        const bool anch = REL && pr.mode == FWD_ANCHORED;
         const uint8_t *__restrict__ bseq = pr.b;
         int2 *__restrict__ bus = pr.bus;
         int *__restrict__ flags = pr.flags;
+        int *stop = anch ? pr.stop_band : nullptr;
         const int need = band - 1;
         const int guard = 32767 - P.max_sub;
+        const int target = pr.target;
+        // dead values of skipped cells, absolute (what the boundary row carries)
+        const int DEAD_H = 0, DEAD_F = anch ? 0 : -go;
 
         const int rb_lo = band * R + lane * RPT;           // first row of the low half
         const int rb_hi = rb_lo + 32 * RPT;                // first row of the high half
@@ -79,39 +112,68 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
             plo[k] = (r0 < n) ? prof[pr.a[r0] & 7] : VIRTUAL_PROF;
             phi[k] = (r1 < n) ? prof[pr.a[r1] & 7] : VIRTUAL_PROF;
         }
-        const uint32_t EB2 = go2;                          // E(i, 0) = -go (local)
-        uint32_t Hl[RPT], E[RPT];
-#pragma unroll
-        for (int k = 0; k < RPT; ++k) { Hl[k] = ZERO2; E[k] = EB2; }
-        uint32_t Hlast = ZERO2, Flast = go2, sellast = 0, updiag = ZERO2;
-        int best_lo = 0, bk_lo = RPT, bc_lo = -1, best_hi = 0, bk_hi = RPT, bc_hi = -1;
-        uint32_t thr = p16(1, 1);                          // report values >= max(best, 1)
-        int published = 0;
-        unsigned tiles = 0, pruned = 0;
-        unsigned long long cells = 0;
-        const int rows_lo = max(0, min(RPT, n - rb_lo)), rows_hi = max(0, min(RPT, n - rb_hi));
         bool aborted = false;
         const int nch = (m + CH - 1) / CH;
         const int nblk = nch + 2;
         const int rows_left = n - band * R;
         {
             int ok = 1;
-            if (lane == 0) ok = wait_flag(&flags[0], need, P.err, nullptr, 0, P.timeout_ns);
+            if (lane == 0) ok = wait_flag(&flags[0], need, P.err, stop, band, P.timeout_ns);
             ok = __shfl_sync(FULL, ok, 0);
             if (!ok) aborted = true;
             else {
-                int2 v = make_int2(0, -go);
+                int2 v = make_int2(DEAD_H, DEAD_F);
                 uint32_t sel = 0;
                 if (lane < m) { v = bus[lane]; sel = sel_lo8(bseq[lane]); }
                 s_in[0][lane] = make_int4(v.x, v.y, (int)sel, 0);
             }
             __syncwarp();
         }
+        if (aborted) continue;
+        // ---- offset, floor and initial state
+        int O = 0;
+        uint32_t fl2 = ZERO2;                              // the local zero floor (relative)
+        if (REL) {
+            int mx0 = INT_MIN;
+            if (lane < m) mx0 = (anch && s_in[0][lane].x < BIAS / 2) ? INT_MIN : s_in[0][lane].x;
+            mx0 = __reduce_max_sync(FULL, mx0);
+            const int border = anch ? (band == 0 ? BIAS : INT_MIN) : 0;
+            const int base = max(mx0, border);
+            // nothing finite yet (anchored, all inputs minus infinity): any offset
+            // works, the first finite input re-centres it
+            O = (base == INT_MIN) ? 0 : base - REL_TOP;
+            const int z = anch ? REL_FLOOR : to_rel(0, O, false);
+            fl2 = p16(z, z);
+            // the chunk enters shared memory in relative form
+            const int4 c = s_in[0][lane];
+            s_in[0][lane] = make_int4(to_rel(c.x, O, anch), to_rel(c.y, O, anch), c.z, 0);
+            __syncwarp();
+        }
+        const int hb = REL ? (anch ? REL_FLOOR : to_rel(0, O, false)) : 0;
+        const int eb = REL ? (anch ? REL_FLOOR : to_rel(-go, O, false)) : -go;
+        uint32_t Hl[RPT], E[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) { Hl[k] = p16(hb, hb); E[k] = p16(eb, eb); }
+        uint32_t Hlast = p16(hb, hb), Flast = p16(eb, eb), sellast = 0;
+        uint32_t updiag = p16(hb, hb);
+        if (REL && anch && band == 0 && lane == 0) updiag = p16(BIAS - O, REL_FLOOR);
+        const int binit = anch ? target - 1 : 0;
+        int best_lo = binit, bk_lo = RPT, bc_lo = -1, best_hi = binit, bk_hi = RPT, bc_hi = -1;
+        auto thr_of = [&](int b) -> int {
+            const long long t = (long long)max(b, binit + 1) - O;
+            return (int)(t > 32767 ? 32767 : (t < -32768 ? -32768 : t));
+        };
+        uint32_t thr = REL ? p16(thr_of(best_lo), thr_of(best_hi)) : p16(1, 1);
+        int published = 0;
+        unsigned tiles = 0, pruned = 0;
+        unsigned long long cells = 0;
+        const int rows_lo = max(0, min(RPT, n - rb_lo)), rows_hi = max(0, min(RPT, n - rb_hi));
+
         for (int q = 0; q < nblk && !aborted; ++q) {
             const int buf = q % 3;
             const bool has_next = (q + 1) < nch;
             int ready = 0;
-            int2 nv = make_int2(0, -go);
+            int2 nv = make_int2(DEAD_H, DEAD_F);
             uint32_t nsel = 0;
             const int ncol = (q + 1) * CH + lane;
             if (has_next) {
@@ -119,21 +181,78 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                 ready = __shfl_sync(FULL, ready, 0);
                 if (ready && ncol < m) { nv = bus[ncol]; nsel = sel_lo8(bseq[ncol]); }
             }
+            // ---- relative mode: re-centre the offset on the window's largest value
+            // (block 0 keeps the offset chosen with chunk 0, which is already relative)
+            if (REL && q > 0) {
+                uint32_t m2 = Hlast;
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) m2 = vmax16(m2, Hl[k]);
+                m2 = vmax16(m2, updiag);
+                int mx = max(lo16(m2), hi16(m2));
+                if (q >= 1 && q < nch) {
+                    // chunk q arrived in absolute form at the end of the last block
+                    const int v = s_in[buf][lane].x;
+                    if (!(anch && v < BIAS / 2)) {
+                        const long long r = (long long)v - O;
+                        mx = max(mx, (int)(r > (1 << 30) ? (1 << 30) : (r < -(1 << 30) ? -(1 << 30) : r)));
+                    }
+                }
+                mx = __reduce_max_sync(FULL, mx);
+                // Re-centre so the largest value sits at REL_TOP.  Every true value of
+                // the window lies within the window spread of that maximum, so it
+                // stays above FLOOR after the shift; whatever falls below FLOOR was a
+                // sentinel (skipped or minus infinity) and stays FLOOR, a value no
+                // larger than the cell's true one.
+                const int d = (mx > REL_FLOOR + 4096) ? mx - REL_TOP : 0;
+                if (d != 0) {
+                    O += d;
+                    if (d >= REL_TOP - REL_FLOOR) {
+                        // everything held was a sentinel: all of it is FLOOR now
+#pragma unroll
+                        for (int k = 0; k < RPT; ++k) { Hl[k] = NEG2; E[k] = NEG2; }
+                        Hlast = NEG2; Flast = NEG2; updiag = NEG2;
+                    } else {
+                        const int lf = max(REL_FLOOR + d, -32768);   // at most FLOOR when d < 0
+                        const uint32_t lift = p16(lf, lf), md = p16(-d, -d);
+                        // x - d, never below FLOOR and never wrapping
+#pragma unroll
+                        for (int k = 0; k < RPT; ++k) {
+                            Hl[k] = __viaddmax_s16x2(vmax16(Hl[k], lift), md, NEG2);
+                            E[k] = __viaddmax_s16x2(vmax16(E[k], lift), md, NEG2);
+                        }
+                        Hlast = __viaddmax_s16x2(vmax16(Hlast, lift), md, NEG2);
+                        Flast = __viaddmax_s16x2(vmax16(Flast, lift), md, NEG2);
+                        updiag = __viaddmax_s16x2(vmax16(updiag, lift), md, NEG2);
+                    }
+                    const int z = anch ? REL_FLOOR : to_rel(0, O, false);
+                    fl2 = p16(z, z);
+                    thr = p16(thr_of(best_lo), thr_of(best_hi));
+                }
+                if (q >= 1 && q < nch) {
+                    const int4 c = s_in[buf][lane];
+                    s_in[buf][lane] = make_int4(to_rel(c.x, O, anch), to_rel(c.y, O, anch), c.z, 0);
+                }
+                __syncwarp();
+            }
             bool skip = false;
             if (P.prune) {
-                int pthr = 0;
-                if (lane == 0) pthr = ld_volatile(pr.best);
-                pthr = __shfl_sync(FULL, pthr, 0);
+                int pthr = target;
+                if (!anch) {
+                    if (lane == 0) pthr = ld_volatile(pr.best);
+                    pthr = __shfl_sync(FULL, pthr, 0);
+                }
                 uint32_t mx2 = Hlast;
 #pragma unroll
-                for (int k = 0; k < RPT; ++k) mx2 = __vimax_s16x2_relu(mx2, Hl[k]);
-                mx2 = __vimax_s16x2_relu(mx2, updiag);
+                for (int k = 0; k < RPT; ++k) mx2 = REL ? vmax16(mx2, Hl[k]) : __vimax_s16x2_relu(mx2, Hl[k]);
+                mx2 = REL ? vmax16(mx2, updiag) : __vimax_s16x2_relu(mx2, updiag);
                 int mx = max(lo16(mx2), hi16(mx2));
                 if (q < nch) mx = max(mx, s_in[buf][lane].x);
                 mx = __reduce_max_sync(FULL, mx);
+                long long mxa = (long long)mx + O;
+                if (!anch) mxa = max(mxa, 0LL);                // a local path may start afresh
                 const int jmin = max(0, q * CH - 2 * CH);
                 const long long rem = (long long)min(rows_left, m - jmin) + 1;
-                skip = (long long)mx + (long long)P.max_sub * rem < (long long)pthr;
+                skip = mxa + (long long)P.max_sub * rem < (long long)pthr;
             }
             ++tiles;
             const bool ramp = (q * CH < 2 * CH) || (q * CH + CH - 1 >= m);
@@ -145,17 +264,19 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
             }
             if (skip) {
                 ++pruned;
+                const int dh = REL ? (anch ? REL_FLOOR : to_rel(0, O, false)) : 0;
+                const int de = REL ? (anch ? REL_FLOOR : to_rel(-go, O, false)) : -go;
 #pragma unroll
-                for (int k = 0; k < RPT; ++k) { Hl[k] = ZERO2; E[k] = EB2; }
-                Hlast = ZERO2;
-                Flast = go2;
+                for (int k = 0; k < RPT; ++k) { Hl[k] = p16(dh, dh); E[k] = p16(de, de); }
+                Hlast = p16(dh, dh);
+                Flast = p16(de, de);
                 // selectors of the columns each half reaches at the end of the block
                 const uint32_t s_lo = (q < nch) ? (uint32_t)s_in[buf][31 - lane].z : 0u;
                 const uint32_t s_hi = (q >= 1 && q - 1 < nch) ? (uint32_t)s_in[(q + 2) % 3][31 - lane].z : 0u;
                 sellast = s_lo | ((s_hi + 0x44u) << 8);
-                updiag = (lane == 0 && q < nch) ? p16(s_in[buf][31].x, 0) : ZERO2;
+                updiag = (lane == 0 && q < nch) ? p16(s_in[buf][31].x, dh) : p16(dh, dh);
                 const int oc = q * CH - 63 + lane;
-                if (oc >= 0 && oc < m) s_out[oc & 63] = make_int2(0, -go);
+                if (oc >= 0 && oc < m) s_out[oc & 63] = make_int2(DEAD_H, DEAD_F);
             } else {
 #pragma unroll 1
                 for (int u = 0; u < CH; ++u) {
@@ -184,19 +305,20 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                         const uint32_t oFlast = Flast;
                         uint32_t hgo = __viaddmax_s16x2(upH, go2, NEG2);   // H(i-1, j) - go
                         uint32_t F = upF;
-                        uint32_t smax = ZERO2;
+                        uint32_t smax = REL ? NEG2 : ZERO2;
                         if (!partial) {
 #pragma unroll
                             for (int k = 0; k < RPT; ++k) {
                                 const uint32_t sc = perm(plo[k], phi[k], sel);
                                 F = __viaddmax_s16x2(F, ge2, hgo);                     // F(i, j)
                                 const uint32_t t = __viaddmax_s16x2(diag, sc, E[k]);   // max(diag + s, E)
-                                const uint32_t h = __vimax3_s16x2_relu(t, F, ZERO2);   // H(i, j)
+                                const uint32_t h = REL ? __vimax3_s16x2(t, F, fl2)     // H(i, j)
+                                                       : __vimax3_s16x2_relu(t, F, ZERO2);
                                 diag = Hl[k];
                                 Hl[k] = h;
                                 hgo = __viaddmax_s16x2(h, go2, NEG2);
                                 E[k] = __viaddmax_s16x2(E[k], ge2, hgo);               // E(i, j+1)
-                                smax = __vimax_s16x2_relu(smax, h);
+                                smax = REL ? vmax16(smax, h) : __vimax_s16x2_relu(smax, h);
                             }
                             Hlast = Hl[RPT - 1];
                             Flast = F;
@@ -206,37 +328,45 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                                 const uint32_t sc = perm(plo[k], phi[k], sel);
                                 F = __viaddmax_s16x2(F, ge2, hgo);
                                 const uint32_t t = __viaddmax_s16x2(diag, sc, E[k]);
-                                const uint32_t h = __vimax3_s16x2_relu(t, F, ZERO2);
+                                const uint32_t h = REL ? __vimax3_s16x2(t, F, fl2)
+                                                       : __vimax3_s16x2_relu(t, F, ZERO2);
                                 diag = Hl[k];
                                 Hl[k] = perm(h, Hl[k], ks);
                                 hgo = __viaddmax_s16x2(h, go2, NEG2);
                                 E[k] = perm(__viaddmax_s16x2(E[k], ge2, hgo), E[k], ks);
-                                smax = __vimax_s16x2_relu(smax, h);
+                                smax = REL ? vmax16(smax, h) : __vimax_s16x2_relu(smax, h);
                             }
-                            smax = perm(smax, 0u, ks);
+                            smax = perm(smax, REL ? NEG2 : 0u, ks);
                             Hlast = Hl[RPT - 1];
                             Flast = perm(F, oFlast, ks);
                         }
                         bool ph, pl;
                         __vibmax_s16x2(smax, thr, &ph, &pl);
                         if (ph || pl) {
-                            const int sl = lo16(smax), sh = hi16(smax);
+                            const int sl = lo16(smax) + O, sh = hi16(smax) + O;
                             if (pl && vlo) {
                                 int kf = RPT;
 #pragma unroll
-                                for (int k = RPT - 1; k >= 0; --k) if (lo16(Hl[k]) == sl) kf = k;
+                                for (int k = RPT - 1; k >= 0; --k) if (lo16(Hl[k]) + O == sl) kf = k;
                                 if (sl > best_lo || (!transposed && kf < bk_lo)) { best_lo = sl; bk_lo = kf; bc_lo = jlo; }
                             }
                             if (ph && vhi) {
                                 int kf = RPT;
 #pragma unroll
-                                for (int k = RPT - 1; k >= 0; --k) if (hi16(Hl[k]) == sh) kf = k;
+                                for (int k = RPT - 1; k >= 0; --k) if (hi16(Hl[k]) + O == sh) kf = k;
                                 if (sh > best_hi || (!transposed && kf < bk_hi)) { best_hi = sh; bk_hi = kf; bc_hi = jhi; }
                             }
-                            thr = p16(max(best_lo, 1), max(best_hi, 1));
-                            if (max(best_lo, best_hi) >= guard && pr.ovf) atomicExch(pr.ovf, 1);
+                            thr = REL ? p16(thr_of(best_lo), thr_of(best_hi)) : p16(max(best_lo, 1), max(best_hi, 1));
+                            if (!REL && max(best_lo, best_hi) >= guard && pr.ovf) atomicExch(pr.ovf, 1);
                         }
-                        if (lane == 31 && vhi) s_out[jhi & 63] = make_int2(hi16(Hlast), hi16(Flast));
+                        if (lane == 31 && vhi) {
+                            int oh = hi16(Hlast), of = hi16(Flast);
+                            if (REL) {
+                                oh = (oh <= REL_FLOOR) ? DEAD_H : oh + O;
+                                of = (of <= REL_FLOOR) ? DEAD_F : of + O;
+                            }
+                            s_out[jhi & 63] = make_int2(oh, of);
+                        }
                     }
                     sellast = sel;
                 }
@@ -244,7 +374,7 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
             if (has_next) {
                 if (!ready) {
                     int ok = 1;
-                    if (lane == 0) ok = wait_flag(&flags[q + 1], need, P.err, nullptr, 0, P.timeout_ns);
+                    if (lane == 0) ok = wait_flag(&flags[q + 1], need, P.err, stop, band, P.timeout_ns);
                     ok = __shfl_sync(FULL, ok, 0);
                     if (!ok) { aborted = true; break; }
                     if (ncol < m) { nv = bus[ncol]; nsel = sel_lo8(bseq[ncol]); }
@@ -258,14 +388,20 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                 __syncwarp();
                 if (lane == 0 && band != P.fault_band) st_release(&flags[q - 2], band);
             }
-            const int wb = __reduce_max_sync(FULL, max(best_lo, best_hi));
-            if (lane == 0 && wb > published) { atomicMax(pr.best, wb); published = wb; }
+            if (!anch) {
+                const int wb = __reduce_max_sync(FULL, max(best_lo, best_hi));
+                if (lane == 0 && wb > published) { atomicMax(pr.best, wb); published = wb; }
+            } else if (stop != nullptr) {
+                int cancel = 0;
+                if (lane == 0) cancel = ld_volatile(stop) < band;
+                if (__shfl_sync(FULL, cancel, 0)) aborted = true;
+            }
         }
         if (aborted) continue;
         // band result over the 64 virtual lanes (low halves hold the smaller rows)
-        int vs = best_lo, vr = rb_lo + (bk_lo < RPT ? bk_lo : 0) + 1, vc = bc_lo + 1, ok = best_lo > 0;
+        int vs = best_lo, vr = rb_lo + (bk_lo < RPT ? bk_lo : 0) + 1, vc = bc_lo + 1, ok = best_lo > binit;
         {
-            const int hs = best_hi, hr = rb_hi + (bk_hi < RPT ? bk_hi : 0) + 1, hc = bc_hi + 1, hok = best_hi > 0;
+            const int hs = best_hi, hr = rb_hi + (bk_hi < RPT ? bk_hi : 0) + 1, hc = bc_hi + 1, hok = best_hi > binit;
             bool take;
             if (!hok) take = false;
             else if (!ok) take = true;
@@ -291,6 +427,7 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
         for (int off = 16; off >= 1; off >>= 1) cells += __shfl_xor_sync(FULL, cells, off);
         if (lane == 0) {
             pr.band_res[band] = make_int4(vs, vr, vc, ok);
+            if (anch && ok && vs == target) atomicMin(pr.stop_band, band);
             atomicAdd(&P.stats[1], (unsigned long long)tiles);
             atomicAdd(&P.stats[2], (unsigned long long)pruned);
             atomicAdd(&P.stats[0], cells);
@@ -298,31 +435,34 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
     }
 }
 
-template <int RPT>
+template <int RPT, bool REL>
 static cudaError_t launch16(const FwdParams &p, int ctas, cudaStream_t s)
 {
-    fwd16_kernel<RPT><<<ctas, 128, 0, s>>>(p);
+    fwd16_kernel<RPT, REL><<<ctas, 128, 0, s>>>(p);
     return cudaGetLastError();
 }
 
 bool fwd16_rpt_supported(int rpt) { return rpt == 4 || rpt == 8 || rpt == 16; }
 
-cudaError_t fwd16_launch(const FwdParams &p, int rpt, int ctas, cudaStream_t s)
+cudaError_t fwd16_launch(const FwdParams &p, int rpt, bool rel, int ctas, cudaStream_t s)
 {
     switch (rpt) {
-    case 4: return launch16<4>(p, ctas, s);
-    case 8: return launch16<8>(p, ctas, s);
-    case 16: return launch16<16>(p, ctas, s);
+    case 4: return rel ? launch16<4, true>(p, ctas, s) : launch16<4, false>(p, ctas, s);
+    case 8: return rel ? launch16<8, true>(p, ctas, s) : launch16<8, false>(p, ctas, s);
+    case 16: return rel ? launch16<16, true>(p, ctas, s) : launch16<16, false>(p, ctas, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t fwd16_occupancy(int rpt, int *n)
+cudaError_t fwd16_occupancy(int rpt, bool rel, int *n)
 {
     switch (rpt) {
-    case 4: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<4>, 128, 0);
-    case 8: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<8>, 128, 0);
-    case 16: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<16>, 128, 0);
+    case 4: return rel ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<4, true>, 128, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<4, false>, 128, 0);
+    case 8: return rel ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<8, true>, 128, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<8, false>, 128, 0);
+    case 16: return rel ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<16, true>, 128, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<16, false>, 128, 0);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -47,8 +47,9 @@ struct FwdParams {
 bool fwd_rpt_supported(int rpt);
 // int16x2 forward kernel (local mode, alphabet <= 4): 64*rpt rows per band
 bool fwd16_rpt_supported(int rpt);
-cudaError_t fwd16_launch(const FwdParams &p, int rpt, int ctas, cudaStream_t s);
-cudaError_t fwd16_occupancy(int rpt, int *ctas_per_sm);
+// rel: values relative to a per-warp offset (long pairs, local and anchored modes)
+cudaError_t fwd16_launch(const FwdParams &p, int rpt, bool rel, int ctas, cudaStream_t s);
+cudaError_t fwd16_occupancy(int rpt, bool rel, int *ctas_per_sm);
 cudaError_t fwd_launch(const FwdParams &p, int rpt, bool two_word_profile, int ctas,
                        int threads, cudaStream_t s);
 cudaError_t fwd_occupancy(int rpt, bool two_word_profile, int threads, int *ctas_per_sm);

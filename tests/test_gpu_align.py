@@ -172,3 +172,35 @@ def test_pair_100k_golden(sw, ctx):
         (g["score"], g["a_begin"], g["a_end"], g["b_begin"], g["b_end"])
     assert len(r.cigar) == g["cigar_len"]
     assert hashlib.sha256(r.cigar.encode()).hexdigest() == g["cigar_sha256"]
+
+
+def test_start_pass_lanes_identical(sw, ctx):
+    """The start-point pass on int16x2 offset lanes equals the int32 pass."""
+    a, b = _gappy_pair(6000, 71)
+    r16 = sw.sw_align(ctx, a, b)
+    ctx.set_option(sw.SW_OPT_FORWARD_LANES, 32)
+    try:
+        r32 = sw.sw_align(ctx, a, b)
+    finally:
+        ctx.set_option(sw.SW_OPT_FORWARD_LANES, 0)
+    assert _tuple(r16) == _tuple(r32) == _tuple(oracle.align(a, b))
+
+
+@pytest.mark.parametrize("rpt", [4, 8, 16])
+def test_offset_lanes_band_heights(sw, ctx, rpt):
+    """int16x2 offset lanes at every band height, pruning on and off: pruned
+    bands whose state is all sentinels must re-centre on the next finite input."""
+    ctx.set_option(sw.SW_OPT_FORWARD_LANES, 16)
+    ctx.set_option(sw.SW_OPT_ROWS_PER_THREAD, rpt)
+    try:
+        for seed, (n, m) in enumerate([(700, 650), (2600, 1500), (1000, 999), (4100, 3900)]):
+            a, b0 = synth.related_pair(max(n, m), seed=n * 31 + m)
+            a, b = a[:n], b0[:m]
+            want = _tuple(oracle.align(a, b))
+            assert _tuple(sw.sw_align(ctx, a, b)) == want
+            assert _tuple(sw.sw_align(ctx, a, b, flags=sw.SW_FLAG_NO_PRUNE)) == want
+        a, b = _gappy_pair(5000, 81)
+        assert _tuple(sw.sw_align(ctx, a, b)) == _tuple(oracle.align(a, b))
+    finally:
+        ctx.set_option(sw.SW_OPT_FORWARD_LANES, 0)
+        ctx.set_option(sw.SW_OPT_ROWS_PER_THREAD, 0)

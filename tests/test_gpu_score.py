@@ -169,3 +169,25 @@ def test_bounded_wait_timeout_is_reported(sw, ctx):
         ctx.set_option(sw.SW_OPT_TIMEOUT_MS, 2000)
     # the context stays usable
     assert _got(sw, ctx, a[:3000], b[:3000]) == _want(a[:3000], b[:3000])
+
+
+@pytest.mark.parametrize("lanes", [16, 32])
+def test_forward_lanes_identical(sw, ctx, lanes):
+    """int16x2 lanes with per-warp offsets and int32 lanes give the same result,
+    including on scores far beyond int16 (the 100 kbp pair scores 41,971)."""
+    ctx.set_option(sw.SW_OPT_FORWARD_LANES, lanes)
+    try:
+        a, b = synth.pair_100k()
+        g = json.load(open(os.path.join(HERE, "golden", "pair_100k.json")))
+        assert _got(sw, ctx, a, b) == (g["score"], g["a_end"], g["b_end"])
+        assert _got(sw, ctx, a, b, flags=sw.SW_FLAG_NO_PRUNE) == (g["score"], g["a_end"], g["b_end"])
+        for seed in range(4):
+            x, y = synth.related_pair(4000 + 777 * seed, seed=300 + seed)
+            assert _got(sw, ctx, x, y) == _want(x, y)
+            assert _got(sw, ctx, y[:2500], x) == _want(y[:2500], x)
+        # a scheme whose value spread does not fit int16 falls back to int32 lanes
+        s = sw.Scheme(40, -30, 60, 20)
+        x, y = synth.related_pair(3000, seed=400)
+        assert _got(sw, ctx, x, y, s) == _want(x, y, oracle.Scheme(40, -30, 60, 20))
+    finally:
+        ctx.set_option(sw.SW_OPT_FORWARD_LANES, 0)
