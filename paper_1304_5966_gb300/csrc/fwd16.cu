@@ -68,11 +68,12 @@ template <int RPT, bool REL>
 __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
 {
     __shared__ int4 s_in_all[4][3][CH];   // {H, F, selector8, 0} per column, three chunks
-    __shared__ int2 s_out_all[4][2 * CH];
+    __shared__ uint32_t s_out_all[4][2 * CH];   // bottom row, packed int16 (H | F << 16)
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     int4 (*s_in)[CH] = s_in_all[wid];
-    int2 *s_out = s_out_all[wid];
+    uint32_t *s_out = s_out_all[wid];
+    const uint32_t pk_in = lane ? 0x3210u : 0x1054u;  // lane 0 splices the band's input in
     const int go = P.go, ge = P.ge;
     const uint32_t go2 = p16(-go, -go), ge2 = p16(-ge, -ge);
     const uint32_t NEG2 = REL ? p16(REL_FLOOR, REL_FLOOR) : p16(-32768, -32768);
@@ -168,6 +169,7 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
         unsigned tiles = 0, pruned = 0;
         unsigned long long cells = 0;
         const int rows_lo = max(0, min(RPT, n - rb_lo)), rows_hi = max(0, min(RPT, n - rb_hi));
+        int O_even = O, O_odd = O;                         // offset used in each block (by parity)
 
         for (int q = 0; q < nblk && !aborted; ++q) {
             const int buf = q % 3;
@@ -234,6 +236,7 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                 }
                 __syncwarp();
             }
+            if (q & 1) O_odd = O; else O_even = O;
             bool skip = false;
             if (P.prune) {
                 int pthr = target;
@@ -276,7 +279,62 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                 sellast = s_lo | ((s_hi + 0x44u) << 8);
                 updiag = (lane == 0 && q < nch) ? p16(s_in[buf][31].x, dh) : p16(dh, dh);
                 const int oc = q * CH - 63 + lane;
-                if (oc >= 0 && oc < m) s_out[oc & 63] = make_int2(DEAD_H, DEAD_F);
+                if (oc >= 0 && oc < m) s_out[oc & 63] = p16(dh, de);
+            } else if (!ramp) {
+                // every lane's two columns are inside the matrix: no validity checks
+#pragma unroll 1
+                for (int u = 0; u < CH; ++u) {
+                    const int s = q * CH + u;
+                    const int4 in = s_in[buf][u];
+                    const uint32_t rH = __shfl_sync(FULL, Hlast, src_lane);
+                    const uint32_t rF = __shfl_sync(FULL, Flast, src_lane);
+                    const uint32_t rS = __shfl_sync(FULL, sellast, src_lane);
+                    const uint32_t upH = perm(rH, lane ? rH : (uint32_t)in.x, pk_in);
+                    const uint32_t upF = perm(rF, lane ? rF : (uint32_t)in.y, pk_in);
+                    const uint32_t sel = lane ? rS : (perm((uint32_t)in.z, rS, 0x0040u) + 0x4400u);
+                    uint32_t diag = updiag;
+                    updiag = upH;
+                    uint32_t hgo = __viaddmax_s16x2(upH, go2, NEG2);       // H(i-1, j) - go
+                    uint32_t F = upF;
+                    uint32_t smax = REL ? NEG2 : ZERO2;
+#pragma unroll
+                    for (int k = 0; k < RPT; ++k) {
+                        const uint32_t sc = perm(plo[k], phi[k], sel);
+                        F = __viaddmax_s16x2(F, ge2, hgo);                     // F(i, j)
+                        const uint32_t t = __viaddmax_s16x2(diag, sc, E[k]);   // max(diag + s, E)
+                        const uint32_t h = REL ? __vimax3_s16x2(t, F, fl2)     // H(i, j)
+                                               : __vimax3_s16x2_relu(t, F, ZERO2);
+                        diag = Hl[k];
+                        Hl[k] = h;
+                        hgo = __viaddmax_s16x2(h, go2, NEG2);
+                        E[k] = __viaddmax_s16x2(E[k], ge2, hgo);               // E(i, j+1)
+                        smax = vmax16(smax, h);                                // running maximum
+                    }
+                    Hlast = Hl[RPT - 1];
+                    Flast = F;
+                    bool ph, pl;
+                    __vibmax_s16x2(smax, thr, &ph, &pl);
+                    if (ph || pl) {
+                        const int jlo = s - lane, jhi = s - lane - 32;
+                        const int sl = lo16(smax) + O, sh = hi16(smax) + O;
+                        if (pl) {
+                            int kf = RPT;
+#pragma unroll
+                            for (int k = RPT - 1; k >= 0; --k) if (lo16(Hl[k]) + O == sl) kf = k;
+                            if (sl > best_lo || (!transposed && kf < bk_lo)) { best_lo = sl; bk_lo = kf; bc_lo = jlo; }
+                        }
+                        if (ph) {
+                            int kf = RPT;
+#pragma unroll
+                            for (int k = RPT - 1; k >= 0; --k) if (hi16(Hl[k]) + O == sh) kf = k;
+                            if (sh > best_hi || (!transposed && kf < bk_hi)) { best_hi = sh; bk_hi = kf; bc_hi = jhi; }
+                        }
+                        thr = REL ? p16(thr_of(best_lo), thr_of(best_hi)) : p16(max(best_lo, 1), max(best_hi, 1));
+                        if (!REL && max(best_lo, best_hi) >= guard && pr.ovf) atomicExch(pr.ovf, 1);
+                    }
+                    if (lane == 31) s_out[(s - 63) & 63] = perm(Hlast, Flast, 0x7632u);
+                    sellast = sel;
+                }
             } else {
 #pragma unroll 1
                 for (int u = 0; u < CH; ++u) {
@@ -359,14 +417,7 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                             thr = REL ? p16(thr_of(best_lo), thr_of(best_hi)) : p16(max(best_lo, 1), max(best_hi, 1));
                             if (!REL && max(best_lo, best_hi) >= guard && pr.ovf) atomicExch(pr.ovf, 1);
                         }
-                        if (lane == 31 && vhi) {
-                            int oh = hi16(Hlast), of = hi16(Flast);
-                            if (REL) {
-                                oh = (oh <= REL_FLOOR) ? DEAD_H : oh + O;
-                                of = (of <= REL_FLOOR) ? DEAD_F : of + O;
-                            }
-                            s_out[jhi & 63] = make_int2(oh, of);
-                        }
+                        if (lane == 31 && vhi) s_out[jhi & 63] = perm(Hlast, Flast, 0x7632u);
                     }
                     sellast = sel;
                 }
@@ -384,7 +435,17 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
             __syncwarp();
             if (q >= 2) {
                 const int col = (q - 2) * CH + lane;
-                if (col < m) bus[col] = s_out[col & 63];
+                if (col < m) {
+                    // column col was written at step col + 63, in block (col + 63) / 32
+                    const uint32_t v = s_out[col & 63];
+                    int oh = lo16(v), of = hi16(v);
+                    if (REL) {
+                        const int Ou = (((col + 63) >> 5) & 1) ? O_odd : O_even;
+                        oh = (oh <= REL_FLOOR) ? DEAD_H : oh + Ou;
+                        of = (of <= REL_FLOOR) ? DEAD_F : of + Ou;
+                    }
+                    bus[col] = make_int2(oh, of);
+                }
                 __syncwarp();
                 if (lane == 0 && band != P.fault_band) st_release(&flags[q - 2], band);
             }
