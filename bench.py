@@ -13,7 +13,8 @@ events on the library's stream; L2 flushed before every step by writing a
 256 MiB buffer); `e2e` is the same call with host (pinned) buffers, the
 host->device copies and the CIGAR read-back inside the timed region.
 `roofline` is for the forward-pass kernel (the dominant one): computed cells
-x 7 integer ops per cell (the minimal DPX cell update) per second, against the
+x 3.5 integer ops per cell (the minimal DPX cell update: 7 ops per int16x2 cell pair)
+per second, against the
 integer pipe's lane rate (64 lane-ops / clock / SM, measured) x SMs x the SM
 clock sampled during the run.  `cpu_baseline` is the CPU oracle (oracle/) on a
 bounded prefix sample of the same pair.  `--impl reference` times that oracle
@@ -35,8 +36,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-OPS_PER_CELL = 7          # minimal int32 DPX cell update
-INT_LANES_PER_CLK = 64    # measured: IMNMX / VIADDMNMX / PRMT lane ops per clock per SM
+OPS_PER_CELL = 3.5        # minimal cell update on int16x2 DPX lanes: 7 ops per two cells
+INT_LANES_PER_CLK = 64    # measured: DPX (32- and 16x2-bit) / PRMT lane ops per clock per SM
 SAMPLE_EDGE = 40_000      # CPU oracle sample: the first 40k x 40k of the pair
 
 
@@ -47,18 +48,25 @@ def _args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-extras", action="store_true", help="skip the batch / plain comparisons")
-    p.add_argument("--workload", default="pair_5m", choices=["pair_5m", "score_500k"],
-                   help="score_500k: forward pass alone on a 500 kbp homologous pair (profiling case)")
+    p.add_argument("--workload", default="pair_5m", choices=["pair_5m", "score_500k", "score_2m"],
+                   help="score_500k / score_2m: forward pass alone on a 500 kbp pair / a 2 Mbp x 1 Mbp "
+                        "homologous pair (profiling cases)")
     p.add_argument("--workspace-gb", type=int, default=0, help="device workspace (default by workload)")
     return p.parse_args()
 
 
 def run_profile_case(args):
-    """Small case for ncu: sw_score on a 500,000 x ~500,000 homologous pair."""
+    """Cases for ncu: sw_score on a 500,000 x ~500,000 homologous pair (score_500k)
+    or on the first 2,000,000 x 1,000,000 of a homologous pair (score_2m, enough
+    bands and columns to fill the band pipeline)."""
     import torch
     import paper_1304_5966_gb300 as sw
     from gen import synth
-    a, b = synth.pair_homologous(500_000, seed=13, gc_permille=410)
+    if args.workload == "score_2m":
+        a, b = synth.pair_homologous(2_000_000, seed=13, gc_permille=410)
+        b = b[:1_000_000].copy()
+    else:
+        a, b = synth.pair_homologous(500_000, seed=13, gc_permille=410)
     ctx = sw.sw_ctx_create(0, workspace_bytes=(args.workspace_gb or 1) << 30)
     ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
     for _ in range(args.warmup):
@@ -67,7 +75,7 @@ def run_profile_case(args):
     for _ in range(args.steps):
         r = sw.sw_score(ctx, ta, tb)
         ms.append(r.stats["ms_forward"])
-    print(json.dumps({"workload": "score_500k", "n": len(a), "m": len(b), "score": r.score,
+    print(json.dumps({"workload": args.workload, "n": len(a), "m": len(b), "score": r.score,
                       "end": [r.a_end, r.b_end], "ms_forward": ms,
                       "gcups": round(len(a) * len(b) / statistics.mean(ms) / 1e6, 1),
                       "fwd_cells": r.stats["fwd_cells"], "tiles_pruned": r.stats["tiles_pruned"],
@@ -251,7 +259,7 @@ def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "score_500k":
+    if args.workload in ("score_500k", "score_2m"):
         return run_profile_case(args)
     ws, rank, local = _dist()
     import numpy as np
@@ -372,7 +380,7 @@ def main():
                    "cigar_len": len(r.cigar or ""), "parallelism": f"replicas x{ws}"},
         "phases_ms": {"forward": round(r.stats["ms_forward"], 1), "start": round(r.stats["ms_start"], 1),
                       "reconstruct": round(r.stats["ms_align"], 1), "levels": r.stats["levels"]},
-        "roofline": {"bound": "alu", "kernel": "fwd_kernel (forward score pass, pruned)",
+        "roofline": {"bound": "alu", "kernel": "fwd16_kernel (forward score pass, int16x2 offset lanes, pruned)",
                      "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
                      "cells_per_launch": int(statistics.mean(fwd_cells)), "ops_per_cell": OPS_PER_CELL,
