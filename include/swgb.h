@@ -91,6 +91,8 @@ typedef struct {
     float ms_forward, ms_start, ms_align;   /* device time per phase */
     int64_t fwd_cells;         /* cells computed by the forward-pass kernel alone */
     int64_t kernel_launches;   /* kernels this call launched */
+    int64_t start_cells;       /* cells computed by the start-point pass */
+    int64_t align_cells;       /* cells computed by the reconstruction label passes */
 } sw_stats;
 
 typedef struct {

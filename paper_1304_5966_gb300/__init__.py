@@ -52,7 +52,8 @@ class _Stats(ctypes.Structure):
                 ("int16_reruns", ctypes.c_int32), ("levels", ctypes.c_int32),
                 ("ms_forward", ctypes.c_float), ("ms_start", ctypes.c_float),
                 ("ms_align", ctypes.c_float), ("fwd_cells", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("start_cells", ctypes.c_int64),
+                ("align_cells", ctypes.c_int64)]
 
 
 class _Result(ctypes.Structure):

@@ -155,7 +155,7 @@ static int run_label_level(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, 
         (e = cudaMemcpyAsync(hst, dstats, sizeof hst, cudaMemcpyDeviceToHost, st)) ||
         (e = cudaStreamSynchronize(st)))
         return set_cuda_error(ctx, e, "label pass");
-    if (stats) stats->cells_computed += (int64_t)hst[0];
+    if (stats) { stats->cells_computed += (int64_t)hst[0]; stats->align_cells += (int64_t)hst[0]; }
     if (herr == DEV_ETIMEOUT) { ctx->last_error = "label pass: device-side wait timed out"; return SW_ETIMEOUT; }
     if (herr) { ctx->last_error = "label pass: device error"; return SW_ECUDA; }
     for (int p = 0; p < np; ++p) {
@@ -411,7 +411,7 @@ int find_start(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const uint8_
     std::vector<int4> res;
     sw_stats tmp{};
     int st = run_forward(ctx, sc, jobs, prune, ctx->opt.rows_per_thread, res, &tmp, ms);
-    if (stats) stats->cells_computed += tmp.cells_computed;
+    if (stats) { stats->cells_computed += tmp.cells_computed; stats->start_cells += tmp.cells_computed; }
     if (st) return st;
     if (!res[0].w || res[0].x != BIAS + S) { ctx->last_error = "internal: start point not found"; return SW_ECUDA; }
     *a_begin = a_end - res[0].y;

@@ -77,7 +77,7 @@ __device__ __forceinline__ int wait_flag(const int *flag, int need, int *err,
             return 0;
         }
         __nanosleep(ns);
-        if (ns < 2048) ns <<= 1;
+        if (ns < 256) ns <<= 1;      // short naps: the awaited chunk is usually microseconds away
     }
 }
 
