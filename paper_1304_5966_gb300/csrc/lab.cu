@@ -30,6 +30,58 @@ __device__ __forceinline__ int border_cost(int k, bool cont, int go, int ge)
     return cont ? ge * k : go + ge * (k - 1);
 }
 
+// Upper bound of the best path value from the source (0,0) through cell (i, j)
+// to the sink (n, m): at most a per diagonal step and at least g per gap column
+// on each side.  Concave and piecewise linear in j (breakpoints j = i and
+// j = i + m - n), so the cells of row i that can still reach the optimum S form
+// one interval, and its ends never decrease from one row to the next.
+__device__ __forceinline__ long long env_bound(long long i, long long j, long long n, long long m,
+                                               long long a, long long g)
+{
+    const long long dr = n - i, dc = m - j;
+    return a * min(i, j) - g * (i > j ? i - j : j - i) + a * min(dr, dc) - g * (dr > dc ? dr - dc : dc - dr);
+}
+
+// First (hi = false) or last (hi = true) DP column of row i whose bound reaches
+// S, or -1 when none does.  The bound peaks at one of j = 0, m, i, i + m - n.
+__device__ __forceinline__ long long env_end(long long i, long long n, long long m, long long a, long long g,
+                                             long long S, bool hi)
+{
+    const long long cand[4] = {0, m, i, i + m - n};
+    long long pj = 0, pv = LLONG_MIN;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const long long j = max(0LL, min(m, cand[k]));
+        const long long v = env_bound(i, j, n, m, a, g);
+        if (v > pv) { pv = v; pj = j; }
+    }
+    if (pv < S) return -1;
+    long long lo = hi ? pj : 0, up = hi ? m : pj;
+    while (lo < up) {
+        const long long md = hi ? (lo + up + 1) >> 1 : (lo + up) >> 1;
+        const bool in = env_bound(i, md, n, m, a, g) >= S;
+        if (hi) { if (in) lo = md; else up = md - 1; }
+        else { if (in) up = md; else lo = md + 1; }
+    }
+    return lo;
+}
+
+// Chunks [first, last] that band b (DP rows bR+1 .. min(n, bR+R)) visits: from
+// the first live column of its first row to the last live column of its last
+// row, one chunk of margin on each side.  Every band's range is computed the
+// same way by the band and by its successor, and both ends are non-decreasing
+// in b, so a chunk a band skips is never overwritten by an earlier band later.
+__device__ __forceinline__ int2 env_band(int b, int R, int n, int m, long long a, long long g, long long S)
+{
+    const int nch = (m + CH - 1) / CH;
+    const long long lo = env_end((long long)b * R + 1, n, m, a, g, S, false);
+    const long long hi = env_end(min((long long)n, (long long)b * R + R), n, m, a, g, S, true);
+    if (lo < 0 || hi < 0) return make_int2(0, nch - 1);
+    // DP column j >= 1 is kernel column j - 1
+    const int qlo = (int)((max(lo, 1LL) - 1) / CH) - 1, qhi = (int)((max(hi, 1LL) - 1) / CH) + 1;
+    return make_int2(max(0, qlo), min(nch - 1, qhi));
+}
+
 template <int RPT, bool PREF_VERT, bool PROF2>
 __global__ void __launch_bounds__(128) lab_kernel(const LabParams P)
 {
@@ -106,33 +158,70 @@ __global__ void __launch_bounds__(128) lab_kernel(const LabParams P)
         unsigned tiles = 0, pruned = 0;
 
         const int nch = (m + CH - 1) / CH;
-        const int nblk = nch + 1;
         const int rows_left = n - band * R;
+        // Static envelope: only cells whose best source-to-sink bound reaches
+        // the target can lie on an optimal path, and such a cell's optimal
+        // predecessors are such cells too, so chunks outside the band's range
+        // are never computed and inputs outside the predecessor's range are
+        // taken as -infinity without waiting for them.
+        int q_lo = 0, q_hi = nch - 1, p_lo = 0, p_hi = nch - 1;
         {
+            const long long S = (long long)pr.target - BIAS;
+            const long long a_sub = P.max_sub, g_min = ge;
+            if (P.prune && pr.target > 0 &&
+                a_sub * min(n, m) - g_min * (n > m ? n - m : m - n) >= S) {
+                const int2 own = env_band(band, R, n, m, a_sub, g_min, S);
+                q_lo = own.x; q_hi = own.y;
+                if (band > 0) {
+                    const int2 pre = env_band(band - 1, R, n, m, a_sub, g_min, S);
+                    p_lo = pre.x; p_hi = pre.y;
+                }
+            }
+        }
+        if (q_lo > 0) {
+            // the band enters at chunk q_lo with everything to its left dead
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) { Hl[k] = 0; E[k] = 0; lHl[k] = LAB_INIT; lE[k] = LAB_INIT; }
+            Hlast = 0; lHlast = LAB_INIT;
+            updiag = 0; lupdiag = LAB_INIT;
+        }
+        {
+            const bool live_in = q_lo >= p_lo && q_lo <= p_hi;
             int ok = 1;
-            if (lane == 0) ok = wait_flag(&flags[0], need, P.err, nullptr, 0, P.timeout_ns);
+            if (lane == 0 && live_in) ok = wait_flag(&flags[q_lo], need, P.err, nullptr, 0, P.timeout_ns);
             ok = __shfl_sync(FULL, ok, 0);
             if (!ok) aborted = true;
             else {
                 int4 v = make_int4(0, 0, LAB_INIT, LAB_INIT);
                 uint32_t sel = 0;
-                if (lane < m) { v = bus[lane]; sel = code_selector(bseq[lane]); }
-                s_in[0][lane] = v;
-                s_sel[0][lane] = sel;
+                const int col = q_lo * CH + lane;
+                if (col < m) {
+                    if (live_in) v = bus[col];
+                    sel = code_selector(bseq[col]);
+                }
+                s_in[q_lo & 1][lane] = v;
+                s_sel[q_lo & 1][lane] = sel;
             }
             __syncwarp();
         }
-        for (int q = 0; q < nblk && !aborted; ++q) {
+        for (int q = q_lo; q <= q_hi + 1 && !aborted; ++q) {
             const int buf = q & 1;
-            const bool has_next = (q + 1) < nch;
+            const bool has_next = q + 1 <= q_hi;
+            const bool next_live = q + 1 >= p_lo && q + 1 <= p_hi;
             int ready = 0;
             int4 nv = make_int4(0, 0, LAB_INIT, LAB_INIT);
             uint32_t nsel = 0;
             const int ncol = (q + 1) * CH + lane;
             if (has_next) {
-                if (lane == 0) ready = ld_acquire(&flags[q + 1]) >= need;
-                ready = __shfl_sync(FULL, ready, 0);
-                if (ready && ncol < m) { nv = bus[ncol]; nsel = code_selector(bseq[ncol]); }
+                ready = 1;
+                if (next_live) {
+                    if (lane == 0) ready = ld_acquire(&flags[q + 1]) >= need;
+                    ready = __shfl_sync(FULL, ready, 0);
+                }
+                if (ready && ncol < m) {
+                    if (next_live) nv = bus[ncol];
+                    nsel = code_selector(bseq[ncol]);
+                }
             }
             bool skip = false;
             if (P.prune && pr.target > 0) {
@@ -140,7 +229,7 @@ __global__ void __launch_bounds__(128) lab_kernel(const LabParams P)
 #pragma unroll
                 for (int k = 0; k < RPT; ++k) mx = max(mx, Hl[k]);
                 mx = max(mx, max(Hlast, updiag));
-                if (q < nch) mx = max(mx, s_in[buf][lane].x);
+                if (q <= q_hi) mx = max(mx, s_in[buf][lane].x);
                 mx = __reduce_max_sync(FULL, mx);
                 // rows / columns still to go from any node this block touches
                 const long long dr_hi = (long long)n - band * R, dr_lo = max(0LL, dr_hi - R);
@@ -158,7 +247,7 @@ __global__ void __launch_bounds__(128) lab_kernel(const LabParams P)
 #pragma unroll
                 for (int k = 0; k < RPT; ++k) { Hl[k] = 0; E[k] = 0; }
                 Hlast = 0; Flast = 0;
-                if (q < nch) {
+                if (q <= q_hi) {
                     sellast = s_sel[buf][31 - lane];
                     updiag = (lane == 0) ? s_in[buf][31].x : 0;
                     lupdiag = (lane == 0) ? s_in[buf][31].z : 0;
@@ -246,7 +335,7 @@ __global__ void __launch_bounds__(128) lab_kernel(const LabParams P)
                 s_sel[buf ^ 1][lane] = nsel;
             }
             __syncwarp();
-            if (q >= 1) {
+            if (q > q_lo) {
                 const int col = (q - 1) * CH + lane;
                 if (col < m) {
                     const int4 o = s_out[col & 63];
