@@ -133,7 +133,11 @@ const char *sw_strerror(int status);
  *   SW_OPT_FORWARD_LANES    single-pair forward and start passes: 0 = int16x2 lanes
  *                           with per-warp offsets when the scheme allows, else int32;
  *                           16 = always try int16x2; 32 = int32 lanes only.  The
- *                           result is identical either way. */
+ *                           result is identical either way.
+ *   SW_OPT_TRACE            1 = print one line per device pass to stderr (kernel
+ *                           time, cells computed, chunks visited and pruned); also
+ *                           switched on at context creation by the environment
+ *                           variable SWGB_TRACE=1. */
 enum {
     SW_OPT_ROWS_PER_THREAD = 1,
     SW_OPT_WARPS_PER_SM = 2,
@@ -141,7 +145,8 @@ enum {
     SW_OPT_FAULT_BAND = 4,
     SW_OPT_CKPT_BANDS = 5,
     SW_OPT_LEAF_CELLS = 6,
-    SW_OPT_FORWARD_LANES = 7
+    SW_OPT_FORWARD_LANES = 7,
+    SW_OPT_TRACE = 8
 };
 int sw_ctx_set_option(sw_ctx *ctx, int option, int64_t value);
 

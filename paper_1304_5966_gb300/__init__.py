@@ -31,7 +31,7 @@ SW_FLAG_NO_PRUNE = 0x4
 SW_FLAG_FORCE_INT32 = 0x8
 SW_FLAG_FORCE_INT16 = 0x10
 SW_OPT_ROWS_PER_THREAD, SW_OPT_WARPS_PER_SM, SW_OPT_TIMEOUT_MS, SW_OPT_FAULT_BAND, \
-    SW_OPT_CKPT_BANDS, SW_OPT_LEAF_CELLS, SW_OPT_FORWARD_LANES = range(1, 8)
+    SW_OPT_CKPT_BANDS, SW_OPT_LEAF_CELLS, SW_OPT_FORWARD_LANES, SW_OPT_TRACE = range(1, 9)
 
 
 class SwError(RuntimeError):

@@ -44,7 +44,7 @@ struct Crossing { int c, type, v, r; };
 static int run_label_level(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const uint8_t *dB,
                            const std::vector<Sub> &subs, const std::vector<int> &trans, bool prune,
                            std::vector<std::vector<Crossing>> &cross, std::vector<int> &sinkv,
-                           sw_stats *stats)
+                           sw_stats *stats, const std::vector<const RootGuide *> &guides)
 {
     const int np = (int)subs.size();
     cross.assign(np, {});
@@ -90,8 +90,20 @@ static int run_label_level(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, 
         maxnck = std::max(maxnck, nck);
         q.bus = s.get<int4>((size_t)km);
         q.flags = s.get<int32_t>((size_t)(km + CH - 1) / CH);
+        q.span = s.get<int2>((size_t)q.nbands);
         q.ckpt = s.get<int4>((size_t)nck * (size_t)km);
         q.sink = s.get<int4>(2);
+        q.gin = nullptr;
+        const RootGuide *rg = guides.empty() ? nullptr : guides[p];
+        if (rg && rg->g && rg->g->valid && !trans[p] && rg->g->step > 0) {
+            // rows recorded by bands that ended before the start point's band
+            const int64_t rows = std::min<int64_t>(rg->g->rows, (rg->e_i - u.a0) / rg->g->step);
+            if (rows > 0) {
+                q.gin = rg->g->buf; q.gin_step = rg->g->step; q.gin_rows = (int32_t)rows;
+                q.gin_nch = rg->g->nch;
+                q.gin_i0 = (int32_t)(rg->e_i + 1 - u.a0); q.gin_j0 = (int32_t)(rg->e_j + 1 - u.b0);
+            }
+        }
         ntk += q.nbands;
     }
     LabProblem *dprobs = s.get<LabProblem>(np);
@@ -131,6 +143,7 @@ static int run_label_level(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, 
         P.prof_hi[x] = tr_launch ? sc.prof_hi_t[x] : sc.prof_hi[x];
     }
     P.go = sc.go; P.ge = sc.ge; P.max_sub = sc.max_sub; P.prune = prune ? 1 : 0;
+    P.slack = std::max(sc.go, -sc.min_sub);
     P.timeout_ns = (unsigned long long)ctx->opt.timeout_ms * 1000000ull;
     const bool p2 = sc.alphabet > 4;
     // problems of both orientations: two launches sharing the ticket counter
@@ -139,6 +152,8 @@ static int run_label_level(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, 
     for (int p = 0; p < np; ++p) (trans[p] ? any_t : any_n) = true;
     if (any_t && any_n) { ctx->last_error = "internal: mixed orientations in one level"; return SW_ECUDA; }
     int per_sm = 1;
+    cudaEvent_t t0 = ctx->ev[8], t1 = ctx->ev[9];
+    if (ctx->opt.trace) cudaEventRecord(t0, st);
     lab_occupancy(!any_t, p2, &per_sm);
     int ctas = std::max(1, per_sm) * ctx->sms;
     ctas = (int)std::min<int64_t>(ctas, (ntk + 3) / 4);
@@ -156,6 +171,17 @@ static int run_label_level(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, 
         (e = cudaStreamSynchronize(st)))
         return set_cuda_error(ctx, e, "label pass");
     if (stats) { stats->cells_computed += (int64_t)hst[0]; stats->align_cells += (int64_t)hst[0]; }
+    if (ctx->opt.trace) {
+        cudaEventRecord(t1, st);
+        cudaEventSynchronize(t1);
+        float kms = 0;
+        cudaEventElapsedTime(&kms, t0, t1);
+        int64_t rows = 0, guided = 0;
+        for (auto &q : hp) { rows += q.n; guided += q.gin != nullptr; }
+        fprintf(stderr, "swgb: label pass: %d problem(s)%s, %lld rows, checkpoint every %d bands, %.2f ms, cells %.4g, chunks %llu pruned %llu%s\n",
+                np, any_t ? " (transposed)" : "", (long long)rows, ck, kms, (double)hst[0], hst[1], hst[2],
+                guided ? ", bounded by the reverse record" : "");
+    }
     if (herr == DEV_ETIMEOUT) { ctx->last_error = "label pass: device-side wait timed out"; return SW_ETIMEOUT; }
     if (herr) { ctx->last_error = "label pass: device error"; return SW_ECUDA; }
     for (int p = 0; p < np; ++p) {
@@ -239,6 +265,8 @@ static int run_leaves(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const
     if (s.failed()) { ctx->last_error = "workspace too small for the leaves"; return SW_ENOMEM; }
     cudaStream_t st = ctx->stream;
     cudaError_t e;
+    cudaEvent_t t0 = ctx->ev[8], t1 = ctx->ev[9];
+    if (ctx->opt.trace) cudaEventRecord(t0, st);
     if ((e = cudaMemcpyAsync(dp, hp.data(), sizeof(LeafProblem) * np, cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(dtab, sc.table, 64, cudaMemcpyHostToDevice, st)) ||
         (e = leaf_launch(dp, np, dtab, sc.go, sc.ge, max_cells, dops, dlen, st)))
@@ -250,6 +278,15 @@ static int run_leaves(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const
         (e = cudaMemcpyAsync(hlen.data(), dlen, sizeof(int32_t) * np, cudaMemcpyDeviceToHost, st)) ||
         (e = cudaStreamSynchronize(st)))
         return set_cuda_error(ctx, e, "leaf pass");
+    if (ctx->opt.trace) {
+        cudaEventRecord(t1, st);
+        cudaEventSynchronize(t1);
+        float kms = 0;
+        cudaEventElapsedTime(&kms, t0, t1);
+        int64_t cells = 0;
+        for (auto &u : subs) cells += (u.n + 1) * (u.m + 1);
+        fprintf(stderr, "swgb: leaves: %d problem(s), %.4g cells, %.2f ms\n", np, (double)cells, kms);
+    }
     for (int p = 0; p < np; ++p) {
         if (hlen[p] < 0) { ctx->last_error = "internal: leaf traceback failed"; return SW_ECUDA; }
         ops[p].assign(hops.data() + hp[p].out_off, (size_t)hlen[p]);
@@ -261,7 +298,7 @@ static int run_leaves(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const
 // H(0,0) and H(n,m) with optimum S.  dA/dB device, hA/hB host copies.
 int reconstruct_many(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const uint8_t *dB,
                      const uint8_t *hA, const uint8_t *hB, const std::vector<Sub> &roots, bool prune,
-                     std::vector<std::string> &ops_out, sw_stats *stats)
+                     std::vector<std::string> &ops_out, sw_stats *stats, const RootGuide *rg)
 {
     std::vector<Seg> segs;
     std::vector<int> owner;                 // root index of every segment
@@ -314,16 +351,23 @@ int reconstruct_many(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const 
             for (int orient = 0; orient < 2; ++orient) {
                 std::vector<Sub> ss;
                 std::vector<int> idx, tr;
+                std::vector<const RootGuide *> gd;
                 for (int k : split_idx) {
                     const Sub &u = segs[k].sub;
-                    const int t = u.m > u.n ? 1 : 0;
+                    // the first root keeps the reverse record while it is whole; it
+                    // is solved in the record's orientation unless that would leave
+                    // too few row bands to fill the GPU
+                    const bool guided = levels == 1 && k == 0 && rg && rg->g && rg->g->valid &&
+                                        (u.m <= u.n || u.n >= 65536);
+                    const int t = (u.m > u.n && !guided) ? 1 : 0;
                     if (t != orient) continue;
                     ss.push_back(u); idx.push_back(k); tr.push_back(t);
+                    gd.push_back(guided ? rg : nullptr);
                 }
                 if (ss.empty()) continue;
                 std::vector<std::vector<Crossing>> cross;
                 std::vector<int> sinkv;
-                int st = run_label_level(ctx, sc, dA, dB, ss, tr, prune, cross, sinkv, stats);
+                int st = run_label_level(ctx, sc, dA, dB, ss, tr, prune, cross, sinkv, stats, gd);
                 if (st) return st;
                 for (size_t x = 0; x < ss.size(); ++x) {
                     if (ss[x].S >= 0 && (int64_t)sinkv[x] != BIAS + ss[x].S) {
@@ -358,11 +402,11 @@ int reconstruct_many(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const 
 
 int reconstruct(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const uint8_t *dB,
                 const uint8_t *hA, const uint8_t *hB, int64_t a0, int64_t n, int64_t b0, int64_t m,
-                int64_t S, bool prune, std::string &ops_out, sw_stats *stats)
+                int64_t S, bool prune, std::string &ops_out, sw_stats *stats, const RootGuide *rg)
 {
     std::vector<Sub> roots(1, Sub{a0, b0, n, m, ST_H, ST_H, S});
     std::vector<std::string> ops;
-    const int st = reconstruct_many(ctx, sc, dA, dB, hA, hB, roots, prune, ops, stats);
+    const int st = reconstruct_many(ctx, sc, dA, dB, hA, hB, roots, prune, ops, stats, rg);
     if (st == SW_OK) ops_out.swap(ops[0]);
     return st;
 }
@@ -397,7 +441,7 @@ char *make_cigar(const std::string &ops, const uint8_t *a, const uint8_t *b, int
 // Start point: reverse anchored pass on A[0, a_end) and B[0, b_end) reversed.
 int find_start(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const uint8_t *dB, int64_t a_end,
                int64_t b_end, int64_t S, bool prune, int64_t *a_begin, int64_t *b_begin, sw_stats *stats,
-               float *ms)
+               float *ms, const Guide *fwd_rec, Guide *rev_rec)
 {
     Scope s(ctx->arena);
     uint8_t *rA = s.get<uint8_t>((size_t)a_end), *rB = s.get<uint8_t>((size_t)b_end);
@@ -408,6 +452,12 @@ int find_start(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const uint8_
     ctx->launches += 2;
     std::vector<FwdJob> jobs(1);
     jobs[0] = {rA, rB, (int32_t)a_end, (int32_t)b_end, FWD_ANCHORED, (int32_t)(BIAS + S), 0};
+    if (prune) {
+        jobs[0].gout = rev_rec;
+        jobs[0].gin = fwd_rec;
+        jobs[0].gin_i0 = (int32_t)(a_end + 1);
+        jobs[0].gin_j0 = (int32_t)(b_end + 1);
+    }
     std::vector<int4> res;
     sw_stats tmp{};
     int st = run_forward(ctx, sc, jobs, prune, ctx->opt.rows_per_thread, res, &tmp, ms);
@@ -425,9 +475,17 @@ int align_one(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const uint8_t
 {
     int64_t S = S_in, ei = ei_in, ej = ej_in;
     int st;
+    // Row records: the forward pass's bounds the start pass's pruning, the start
+    // pass's bounds the first reconstruction level's.  Each may take a sixth
+    // of the free workspace; without room a pass runs without its record.
+    Scope keep(ctx->arena);
+    Guide fwd_rec, rev_rec;
+    fwd_rec.scope = &keep; fwd_rec.budget = ctx->arena.largest_free() / 6;
+    rev_rec.scope = &keep;
     if (!have_score) {
         std::vector<FwdJob> jobs(1);
         jobs[0] = {dA, dB, (int32_t)n, (int32_t)m, FWD_LOCAL, 0, 0};
+        if (prune) jobs[0].gout = &fwd_rec;
         std::vector<int4> res;
         float ms = 0;
         st = run_forward(ctx, sc, jobs, prune, ctx->opt.rows_per_thread, res, &out->stats, &ms);
@@ -442,11 +500,17 @@ int align_one(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const uint8_t
     cudaEventRecord(e0, ctx->stream);
     int64_t ab = -1, bb = -1;
     float ms_start = 0;
-    if ((st = find_start(ctx, sc, dA, dB, ei, ej, S, prune, &ab, &bb, &out->stats, &ms_start))) return st;
+    rev_rec.budget = ctx->arena.largest_free() / 6;
+    if ((st = find_start(ctx, sc, dA, dB, ei, ej, S, prune, &ab, &bb, &out->stats, &ms_start, &fwd_rec,
+                         &rev_rec)))
+        return st;
     cudaEventRecord(e1, ctx->stream);
     out->a_begin = ab; out->b_begin = bb;
     std::string ops;
-    if ((st = reconstruct(ctx, sc, dA, dB, hA, hB, ab, ei - ab, bb, ej - bb, S, prune, ops, &out->stats)))
+    RootGuide rg;
+    rg.g = &rev_rec; rg.e_i = ei; rg.e_j = ej;
+    if ((st = reconstruct(ctx, sc, dA, dB, hA, hB, ab, ei - ab, bb, ej - bb, S, prune, ops, &out->stats,
+                          prune ? &rg : nullptr)))
         return st;
     cudaEventRecord(e2, ctx->stream);
     cudaEventSynchronize(e2);

@@ -108,7 +108,9 @@ static int auto_rpt16(sw_ctx *ctx, const std::vector<FwdJob> &jobs, bool rel, co
     for (int k = 0; k < 3; ++k) {
         if (rel && !rel16_fits(sc, cands[k])) continue;
         int per_sm = 1;
-        if (fwd16_occupancy(cands[k], rel, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+        if (fwd16_occupancy(cands[k], rel, rel && jobs[0].mode == FWD_ANCHORED, &per_sm) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
         const double warps = 4.0 * per_sm * ctx->sms;
         int64_t bands = 0, rows = 0;
         for (auto &j : jobs) { bands += (j.n + 64 * cands[k] - 1) / (64 * cands[k]); rows += j.n; }
@@ -140,6 +142,29 @@ static int run_forward_impl(sw_ctx *ctx, const SchemeDev &sc, const std::vector<
         q.bus = sc_.get<int2>((size_t)j.m);
         q.flags = sc_.get<int32_t>((size_t)(j.m + CH - 1) / CH);
         q.band_res = sc_.get<int4>((size_t)q.nbands);
+        q.span = sc_.get<int2>((size_t)q.nbands);
+        q.gout = nullptr; q.gstride = 1; q.gnch = 0;
+        q.gin = nullptr; q.gin_step = 1; q.gin_rows = 0; q.gin_nch = 0; q.gin_i0 = 0; q.gin_j0 = 0;
+        if (lane16 && rel && j.gout && j.gout->scope) {
+            // every band's row when the budget allows, else every stride-th
+            Guide &g = *j.gout;
+            g.valid = false;
+            const int64_t nch = (j.m + CH - 1) / CH;
+            int64_t stride = 1;
+            while (stride < q.nbands && (q.nbands / stride) * (nch + 2) * 4 > (int64_t)g.budget) ++stride;
+            const int64_t rows = q.nbands / stride;
+            if (rows > 0 && rows * (nch + 2) * 4 <= (int64_t)g.budget) {
+                g.buf = g.scope->get<int32_t>((size_t)(rows * (nch + 2)));
+                if (g.buf) {
+                    g.step = (int32_t)(stride * R); g.rows = (int32_t)rows; g.nch = (int32_t)nch;
+                    q.gout = g.buf; q.gstride = (int32_t)stride; q.gnch = (int32_t)nch;
+                }
+            }
+        }
+        if (lane16 && rel && j.gin && j.gin->valid && j.mode == FWD_ANCHORED) {
+            q.gin = j.gin->buf; q.gin_step = j.gin->step; q.gin_rows = j.gin->rows; q.gin_nch = j.gin->nch;
+            q.gin_i0 = j.gin_i0; q.gin_j0 = j.gin_j0;
+        }
         ntk += q.nbands;
     }
     int32_t *ctrs = sc_.get<int32_t>(4 * (size_t)np + 8);      // best, stop, ovf per problem + globals
@@ -201,6 +226,7 @@ static int run_forward_impl(sw_ctx *ctx, const SchemeDev &sc, const std::vector<
         P.prof_lo_t[x] = sc.prof_lo_t[x]; P.prof_hi_t[x] = sc.prof_hi_t[x];
     }
     P.go = sc.go; P.ge = sc.ge; P.max_sub = sc.max_sub;
+    P.slack = std::max(sc.go, -sc.min_sub);
     P.prune = prune ? 1 : 0;
     P.fault_band = ctx->opt.fault_band;
     P.timeout_ns = (unsigned long long)ctx->opt.timeout_ms * 1000000ull;
@@ -208,7 +234,7 @@ static int run_forward_impl(sw_ctx *ctx, const SchemeDev &sc, const std::vector<
     int ctas;
     if (lane16) {
         int per_sm = 1;
-        if (fwd16_occupancy(rpt, rel, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+        if (fwd16_occupancy(rpt, rel, rel && anch, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
         if (ctx->opt.warps_per_sm > 0) per_sm = std::max(1, std::min(per_sm, ctx->opt.warps_per_sm / 4));
         ctas = per_sm * ctx->sms;
     } else {
@@ -216,7 +242,7 @@ static int run_forward_impl(sw_ctx *ctx, const SchemeDev &sc, const std::vector<
     }
     ctas = (int)std::min<int64_t>(ctas, (ntk + 3) / 4);
     cudaEventRecord(ctx->ev[0], s);
-    if ((e = lane16 ? fwd16_launch(P, rpt, rel, ctas, s) : fwd_launch(P, rpt, p2, ctas, 128, s)))
+    if ((e = lane16 ? fwd16_launch(P, rpt, rel, rel && anch, ctas, s) : fwd_launch(P, rpt, p2, ctas, 128, s)))
         return set_cuda_error(ctx, e, "forward launch");
     cudaEventRecord(ctx->ev[1], s);
     if ((e = fwd_reduce_launch(dprobs, np, dres, s))) return set_cuda_error(ctx, e, "forward reduce");
@@ -235,6 +261,14 @@ static int run_forward_impl(sw_ctx *ctx, const SchemeDev &sc, const std::vector<
         return set_cuda_error(ctx, e, "forward pass");
     ctx->launches += 3;
     if (ms) cudaEventElapsedTime(ms, ctx->ev[0], ctx->ev[1]);
+    if (ctx->opt.trace) {
+        float kms = 0;
+        cudaEventElapsedTime(&kms, ctx->ev[0], ctx->ev[1]);
+        fprintf(stderr, "swgb: %s pass: %d problem(s), %s lanes, %d rows/band, %.2f ms, cells %.4g, chunks %llu pruned %llu%s%s\n",
+                anch ? "anchored" : "local", np, lane16 ? (rel ? "int16x2 offset" : "int16x2") : "int32", R, kms,
+                (double)hst[0], hst[1], hst[2], hp[0].gout ? ", recording rows" : "",
+                hp[0].gin ? ", bounded by the forward record" : "");
+    }
     if (stats) {
         if (jobs[0].mode == FWD_LOCAL) stats->fwd_cells += (int64_t)hst[0];
         stats->cells_computed += (int64_t)hst[0];
@@ -245,6 +279,8 @@ static int run_forward_impl(sw_ctx *ctx, const SchemeDev &sc, const std::vector<
     if (herr) { ctx->last_error = "device error word set"; return SW_ECUDA; }
     if (ovf)
         for (int p = 0; p < np; ++p) (*ovf)[p] = hctr[3 * (size_t)p + 2] != 0;
+    for (int p = 0; p < np; ++p)
+        if (hp[p].gout) jobs[p].gout->valid = !(ovf && (*ovf)[p]);
     return SW_OK;
 }
 
@@ -378,6 +414,7 @@ int sw_ctx_create(int device, void *stream, void *workspace, uint64_t workspace_
     c->ws_bytes = workspace_bytes;
     c->arena.reset(c->ws, workspace_bytes);
     for (auto &ev : c->ev) cudaEventCreate(&ev);
+    if (const char *t = getenv("SWGB_TRACE")) c->opt.trace = (t[0] == '1');
     *out = c;
     return SW_OK;
 }
@@ -416,6 +453,9 @@ int sw_ctx_set_option(sw_ctx *ctx, int option, int64_t value)
     case SW_OPT_FORWARD_LANES:
         if (value != 0 && value != 16 && value != 32) return SW_EINVAL;
         ctx->opt.forward_lanes = (int)value; return SW_OK;
+    case SW_OPT_TRACE:
+        if (value != 0 && value != 1) return SW_EINVAL;
+        ctx->opt.trace = (int)value; return SW_OK;
     case SW_OPT_LEAF_CELLS:
         if (value < 256 || value > (1 << 18)) return SW_EINVAL;
         ctx->opt.leaf_cells = value; return SW_OK;

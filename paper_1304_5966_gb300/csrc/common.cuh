@@ -5,6 +5,7 @@
 // accessors for the inter-band progress flags, and the bounded wait that
 // every inter-warp dependency goes through.
 #pragma once
+#include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -79,6 +80,46 @@ __device__ __forceinline__ int wait_flag(const int *flag, int need, int *err,
         __nanosleep(ns);
         if (ns < 256) ns <<= 1;      // short naps: the awaited chunk is usually microseconds away
     }
+}
+
+// Published-range words (the first and last useful chunk of a band, see the
+// label and anchored passes): not yet written, and "no useful chunk".
+constexpr int SPAN_UNPUB = INT_MIN;
+constexpr int SPAN_NONE = INT_MAX;
+
+// Bounded wait until *p holds a published value (not SPAN_UNPUB).  Called by
+// one lane; returns 1 with the value in *out, or 0 when the error word is set
+// or the wait ran past limit_ns (then it records DEV_ETIMEOUT).
+// Also returns 0 (without recording anything) when `*cancel` drops below
+// cancel_above.
+__device__ __forceinline__ int wait_published(const int *p, int *err, unsigned long long limit_ns, int *out,
+                                              const int *cancel = nullptr, int cancel_above = 0) {
+    int v = ld_acquire(p);
+    if (v != SPAN_UNPUB) { *out = v; return 1; }
+    const unsigned long long t0 = globaltimer();
+    unsigned ns = 64;
+    for (;;) {
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+        v = ld_acquire(p);
+        if (v != SPAN_UNPUB) { *out = v; return 1; }
+        if (ld_volatile(err)) return 0;
+        if (cancel && ld_volatile(cancel) < cancel_above) return 0;
+        if (globaltimer() - t0 > limit_ns) {
+            atomicCAS(err, 0, DEV_ETIMEOUT);
+            return 0;
+        }
+    }
+}
+
+// Record row of running maxima (see FwdProblem::gout): nch entries, then the
+// first and last chunk the band wrote.  Chunks before the first hold nothing
+// (0: minus infinity biased, or the local zero); chunks after the last hold
+// the row's final maximum.
+__device__ __forceinline__ int rec_at(const int32_t *row, int nch, int c) {
+    const int lo = row[nch], hi = row[nch + 1];
+    if (hi < lo || c < lo) return 0;
+    return row[min(c, hi)];
 }
 
 }  // namespace swgb

@@ -109,6 +109,7 @@ struct Options {
     int ckpt_bands = 0;            // 0 = choose from the workspace size
     int64_t leaf_cells = 1 << 16;
     int forward_lanes = 0;         // 0 auto, 16 int16x2 (offset) lanes, 32 int32 lanes
+    int trace = 0;                 // 1: one stderr line per device pass
 };
 
 }  // namespace swgb
@@ -123,7 +124,7 @@ struct sw_ctx {
     swgb::Arena arena;
     swgb::Options opt;
     std::string last_error;
-    cudaEvent_t ev[8] = {};
+    cudaEvent_t ev[10] = {};
     std::mutex call_mu;
     int64_t launches = 0;          // kernels launched by this context (all calls)
 };
@@ -135,6 +136,18 @@ int build_scheme(const sw_scheme *s, SchemeDev *out);
 
 // Forward pass over a set of problems (one persistent launch).  res[p] receives
 // {score, row, col, found} (biased in anchored mode).  stats may be null.
+// Row record of a forward or anchored pass (see FwdProblem::gout): running
+// column maxima of every stride-th band's bottom row, kept by the caller for
+// the next pass over the same pair.
+struct Guide {
+    Scope *scope = nullptr;    // where the pass allocates the record
+    size_t budget = 0;         // bytes it may take there
+    int32_t *buf = nullptr;    // rows x (nch + 2), rows read with rec_at
+    int32_t step = 0;          // DP rows between recorded rows
+    int32_t rows = 0, nch = 0;
+    bool valid = false;        // set when the pass wrote it (int16x2 offset lanes, no re-run)
+};
+
 struct FwdJob {
     const uint8_t *a;      // device
     const uint8_t *b;      // device
@@ -142,6 +155,9 @@ struct FwdJob {
     int32_t mode;          // FwdMode
     int32_t target;        // anchored: biased target
     int32_t transposed;
+    Guide *gout = nullptr;         // record this pass's rows here
+    const Guide *gin = nullptr;    // anchored: forward record to prune with
+    int32_t gin_i0 = 0, gin_j0 = 0;
 };
 int run_forward(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &jobs, bool prune,
                 int rpt, std::vector<int4> &res, sw_stats *stats, float *ms);

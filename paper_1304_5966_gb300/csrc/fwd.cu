@@ -285,7 +285,10 @@ __global__ void fwd_init_kernel(FwdProblem *probs, int nprobs, int h0, int f0)
     for (int j = threadIdx.x; j < pr.m; j += blockDim.x) pr.bus[j] = make_int2(h0, f0);
     const int nch = (pr.m + CH - 1) / CH;
     for (int c = threadIdx.x; c < nch; c += blockDim.x) pr.flags[c] = -1;
-    for (int b = threadIdx.x; b < pr.nbands; b += blockDim.x) pr.band_res[b] = make_int4(0, 0, 0, 0);
+    for (int b = threadIdx.x; b < pr.nbands; b += blockDim.x) {
+        pr.band_res[b] = make_int4(0, 0, 0, 0);
+        if (pr.span) pr.span[b] = make_int2(SPAN_UNPUB, SPAN_UNPUB);
+    }
     if (threadIdx.x == 0) {
         if (pr.best) *pr.best = 0;
         if (pr.stop_band) *pr.stop_band = 0x7fffffff;

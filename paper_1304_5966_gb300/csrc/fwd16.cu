@@ -49,6 +49,9 @@ __device__ __forceinline__ uint32_t perm(uint32_t a, uint32_t b, uint32_t s) {
 // the high half's selector is the same plus 0x44 (bytes 4-7)
 __device__ __forceinline__ uint32_t sel_lo8(uint32_t c) { return c | ((c | 8u) << 4); }
 
+// a valid selector pair (code 0 for both halves)
+constexpr uint32_t SEL_NEUTRAL = (0u | (8u << 4)) | (((0u | (8u << 4)) + 0x44u) << 8);
+
 // per-halfword max of two (DPX three-input form with a repeated operand)
 __device__ __forceinline__ uint32_t vmax16(uint32_t a, uint32_t b) { return __vimax3_s16x2(a, b, b); }
 
@@ -64,7 +67,7 @@ __device__ __forceinline__ int to_rel(int v, int O, bool anch)
     return (int)(r < REL_FLOOR ? REL_FLOOR : (r > 32767 ? 32767 : r));
 }
 
-template <int RPT, bool REL>
+template <int RPT, bool REL, bool ANCH>
 __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
 {
     __shared__ int4 s_in_all[4][3][CH];   // {H, F, selector8, 0} per column, three chunks
@@ -92,7 +95,7 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
         const int band = tb.y;
         const int n = pr.n, m = pr.m;
         const bool transposed = pr.transposed != 0;
-        const bool anch = REL && pr.mode == FWD_ANCHORED;
+        constexpr bool anch = REL && ANCH;    // every problem of an anchored launch is anchored
         const uint8_t *__restrict__ bseq = pr.b;
         int2 *__restrict__ bus = pr.bus;
         int *__restrict__ flags = pr.flags;
@@ -117,16 +120,75 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
         const int nch = (m + CH - 1) / CH;
         const int nblk = nch + 2;
         const int rows_left = n - band * R;
-        {
-            int ok = 1;
-            if (lane == 0) ok = wait_flag(&flags[0], need, P.err, stop, band, P.timeout_ns);
+        // Dynamic range (anchored with pruning): every band marks each chunk it
+        // releases as useful or not (low bit of the flag: can a value of the
+        // chunk still reach the target from the next band?) and publishes its
+        // first and last useful chunk.  Below the anchor the left border is
+        // minus infinity, so the next band starts at the first useful chunk,
+        // takes everything else as minus infinity without waiting for it and
+        // stops once a pruned block has nothing useful left from its column on.
+        const bool dyn = anch && P.prune;
+        int pfirst = 0;
+        const int *pred_last = nullptr;
+        if (dyn && band > 0) {
+            int pf = 0, ok = 1;
+            if (lane == 0) ok = wait_published(&pr.span[band - 1].x, P.err, P.timeout_ns, &pf, stop, band);
             ok = __shfl_sync(FULL, ok, 0);
-            if (!ok) aborted = true;
+            pf = __shfl_sync(FULL, pf, 0);
+            if (!ok) continue;                // error, or the search already ended above
+            pfirst = pf;
+            pred_last = &pr.span[band - 1].y;
+        }
+        const int L = pfirst;
+        if (L >= nch) {
+            // nothing from above can reach the target: neither can this band
+            if (lane == 0) {
+                st_release(&pr.span[band].x, SPAN_NONE);
+                st_release(&pr.span[band].y, -1);
+            }
+            continue;
+        }
+        // input chunk c: 1 useful (read the bus), 0 dead, 2 not released yet
+        auto in_status = [&](int c) -> int {
+            if (c < pfirst) return 0;
+            const int v = ld_acquire(&flags[c]);
+            if (v >= 2 * need) return v & 1;
+            if (pred_last) {
+                const int y = ld_acquire(pred_last);
+                if (y != SPAN_UNPUB && c > y) return 0;
+            }
+            return 2;
+        };
+        // the same, waiting (bounded) for the release; -1 when the band must stop
+        auto wait_status = [&](int c) -> int {
+            int st = in_status(c);
+            if (st != 2) return st;
+            const unsigned long long t0 = globaltimer();
+            unsigned ns = 64;
+            for (;;) {
+                __nanosleep(ns);
+                if (ns < 256) ns <<= 1;
+                st = in_status(c);
+                if (st != 2) return st;
+                if (ld_volatile(P.err)) return -1;
+                if (stop && ld_volatile(stop) < band) return -1;
+                if (globaltimer() - t0 > P.timeout_ns) { atomicCAS(P.err, 0, DEV_ETIMEOUT); return -1; }
+            }
+        };
+        {
+            int st = 0;
+            if (lane == 0) st = wait_status(L);
+            st = __shfl_sync(FULL, st, 0);
+            if (st < 0) aborted = true;
             else {
                 int2 v = make_int2(DEAD_H, DEAD_F);
                 uint32_t sel = 0;
-                if (lane < m) { v = bus[lane]; sel = sel_lo8(bseq[lane]); }
-                s_in[0][lane] = make_int4(v.x, v.y, (int)sel, 0);
+                const int col = L * CH + lane;
+                if (col < m) {
+                    if (st == 1) v = bus[col];
+                    sel = sel_lo8(bseq[col]);
+                }
+                s_in[L % 3][lane] = make_int4(v.x, v.y, (int)sel, 0);
             }
             __syncwarp();
         }
@@ -136,7 +198,7 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
         uint32_t fl2 = ZERO2;                              // the local zero floor (relative)
         if (REL) {
             int mx0 = INT_MIN;
-            if (lane < m) mx0 = (anch && s_in[0][lane].x < BIAS / 2) ? INT_MIN : s_in[0][lane].x;
+            if (L * CH + lane < m) mx0 = (anch && s_in[L % 3][lane].x < BIAS / 2) ? INT_MIN : s_in[L % 3][lane].x;
             mx0 = __reduce_max_sync(FULL, mx0);
             const int border = anch ? (band == 0 ? BIAS : INT_MIN) : 0;
             const int base = max(mx0, border);
@@ -146,8 +208,8 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
             const int z = anch ? REL_FLOOR : to_rel(0, O, false);
             fl2 = p16(z, z);
             // the chunk enters shared memory in relative form
-            const int4 c = s_in[0][lane];
-            s_in[0][lane] = make_int4(to_rel(c.x, O, anch), to_rel(c.y, O, anch), c.z, 0);
+            const int4 c = s_in[L % 3][lane];
+            s_in[L % 3][lane] = make_int4(to_rel(c.x, O, anch), to_rel(c.y, O, anch), c.z, 0);
             __syncwarp();
         }
         const int hb = REL ? (anch ? REL_FLOOR : to_rel(0, O, false)) : 0;
@@ -155,7 +217,10 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
         uint32_t Hl[RPT], E[RPT];
 #pragma unroll
         for (int k = 0; k < RPT; ++k) { Hl[k] = p16(hb, hb); E[k] = p16(eb, eb); }
-        uint32_t Hlast = p16(hb, hb), Flast = p16(eb, eb), sellast = 0;
+        // Selectors reach a lane from the one above it, so cells left of the
+        // band's first column start from this one: any valid selector (sign
+        // extension included) keeps their scores in the profile's range.
+        uint32_t Hlast = p16(hb, hb), Flast = p16(eb, eb), sellast = SEL_NEUTRAL;
         uint32_t updiag = p16(hb, hb);
         if (REL && anch && band == 0 && lane == 0) updiag = p16(BIAS - O, REL_FLOOR);
         const int binit = anch ? target - 1 : 0;
@@ -167,31 +232,57 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
         uint32_t thr = REL ? p16(thr_of(best_lo), thr_of(best_hi)) : p16(1, 1);
         int published = 0;
         unsigned tiles = 0, pruned = 0;
+        // row record of this band's bottom row (running maximum over chunks)
+        int32_t *grow = (pr.gout && (band + 1) % pr.gstride == 0)
+                            ? pr.gout + (size_t)((band + 1) / pr.gstride - 1) * (size_t)(pr.gnch + 2) : nullptr;
+        int grun = INT_MIN;
+        // Anchored with the forward record: any path through a cell of this band
+        // that reaches the start crosses a recorded forward row r at or above the
+        // band (or starts below it), so what it gains beyond the band's frontier
+        // is at most max_sub per row from the frontier up to r, plus the largest
+        // forward H of row r left of the cell's column (plus the slack of the
+        // split cell).  Row 0 of the forward matrix is all zero.
+        const int32_t *gin_row = nullptr;
+        long long gin_gain = 0;
+        if (anch && pr.gin) {
+            const long long T = max(1LL, (long long)pr.gin_i0 - (long long)(band + 1) * R);
+            long long k = T / pr.gin_step - 1;
+            if (k > pr.gin_rows - 1) k = pr.gin_rows - 1;
+            const long long r = k >= 0 ? (k + 1) * (long long)pr.gin_step : 0;
+            if (k >= 0) gin_row = pr.gin + (size_t)k * (size_t)(pr.gin_nch + 2);
+            gin_gain = (long long)P.max_sub * ((long long)pr.gin_i0 - (long long)band * R - r) + P.slack;
+        }
         unsigned long long cells = 0;
         const int rows_lo = max(0, min(RPT, n - rb_lo)), rows_hi = max(0, min(RPT, n - rb_hi));
         int O_even = O, O_odd = O;                         // offset used in each block (by parity)
 
-        for (int q = 0; q < nblk && !aborted; ++q) {
+        bool first_pub = false;
+        int last_useful = -1, last_flushed = -1;
+        for (int q = L; q < nblk && !aborted; ++q) {
             const int buf = q % 3;
             const bool has_next = (q + 1) < nch;
-            int ready = 0;
+            int nst = 0;
             int2 nv = make_int2(DEAD_H, DEAD_F);
             uint32_t nsel = 0;
             const int ncol = (q + 1) * CH + lane;
             if (has_next) {
-                if (lane == 0) ready = ld_acquire(&flags[q + 1]) >= need;
-                ready = __shfl_sync(FULL, ready, 0);
-                if (ready && ncol < m) { nv = bus[ncol]; nsel = sel_lo8(bseq[ncol]); }
+                if (lane == 0) nst = in_status(q + 1);
+                nst = __shfl_sync(FULL, nst, 0);
+                if (nst != 2 && ncol < m) {
+                    if (nst == 1) nv = bus[ncol];
+                    nsel = sel_lo8(bseq[ncol]);
+                }
             }
             // ---- relative mode: re-centre the offset on the window's largest value
-            // (block 0 keeps the offset chosen with chunk 0, which is already relative)
-            if (REL && q > 0) {
+            // (the first block keeps the offset chosen with its chunk, which is
+            // already relative)
+            if (REL && q > L) {
                 uint32_t m2 = Hlast;
 #pragma unroll
                 for (int k = 0; k < RPT; ++k) m2 = vmax16(m2, Hl[k]);
                 m2 = vmax16(m2, updiag);
                 int mx = max(lo16(m2), hi16(m2));
-                if (q >= 1 && q < nch) {
+                if (q < nch) {
                     // chunk q arrived in absolute form at the end of the last block
                     const int v = s_in[buf][lane].x;
                     if (!(anch && v < BIAS / 2)) {
@@ -230,7 +321,7 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                     fl2 = p16(z, z);
                     thr = p16(thr_of(best_lo), thr_of(best_hi));
                 }
-                if (q >= 1 && q < nch) {
+                if (q < nch) {
                     const int4 c = s_in[buf][lane];
                     s_in[buf][lane] = make_int4(to_rel(c.x, O, anch), to_rel(c.y, O, anch), c.z, 0);
                 }
@@ -256,6 +347,14 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                 const int jmin = max(0, q * CH - 2 * CH);
                 const long long rem = (long long)min(rows_left, m - jmin) + 1;
                 skip = mxa + (long long)P.max_sub * rem < (long long)pthr;
+                if (!skip && anch && pr.gin) {
+                    // largest forward column of the block's cells, and the record
+                    // of row r up to it
+                    const int jf = pr.gin_j0 - max(1, q * CH - 62);
+                    long long pm = 0;
+                    if (gin_row && jf >= 1) pm = rec_at(gin_row, pr.gin_nch, min(pr.gin_nch - 1, (jf - 1) / CH));
+                    skip = mxa + gin_gain + pm < (long long)pthr;
+                }
             }
             ++tiles;
             const bool ramp = (q * CH < 2 * CH) || (q * CH + CH - 1 >= m);
@@ -274,8 +373,8 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                 Hlast = p16(dh, dh);
                 Flast = p16(de, de);
                 // selectors of the columns each half reaches at the end of the block
-                const uint32_t s_lo = (q < nch) ? (uint32_t)s_in[buf][31 - lane].z : 0u;
-                const uint32_t s_hi = (q >= 1 && q - 1 < nch) ? (uint32_t)s_in[(q + 2) % 3][31 - lane].z : 0u;
+                const uint32_t s_lo = (q < nch) ? (uint32_t)s_in[buf][31 - lane].z : sel_lo8(0);
+                const uint32_t s_hi = (q > L && q - 1 < nch) ? (uint32_t)s_in[(q + 2) % 3][31 - lane].z : sel_lo8(0);
                 sellast = s_lo | ((s_hi + 0x44u) << 8);
                 updiag = (lane == 0 && q < nch) ? p16(s_in[buf][31].x, dh) : p16(dh, dh);
                 const int oc = q * CH - 63 + lane;
@@ -423,18 +522,23 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                 }
             }
             if (has_next) {
-                if (!ready) {
-                    int ok = 1;
-                    if (lane == 0) ok = wait_flag(&flags[q + 1], need, P.err, stop, band, P.timeout_ns);
-                    ok = __shfl_sync(FULL, ok, 0);
-                    if (!ok) { aborted = true; break; }
-                    if (ncol < m) { nv = bus[ncol]; nsel = sel_lo8(bseq[ncol]); }
+                if (nst == 2) {
+                    int st = 0;
+                    if (lane == 0) st = wait_status(q + 1);
+                    st = __shfl_sync(FULL, st, 0);
+                    if (st < 0) { aborted = true; break; }
+                    if (ncol < m) {
+                        if (st == 1) nv = bus[ncol];
+                        nsel = sel_lo8(bseq[ncol]);
+                    }
                 }
                 s_in[(q + 1) % 3][lane] = make_int4(nv.x, nv.y, (int)nsel, 0);
             }
             __syncwarp();
-            if (q >= 2) {
-                const int col = (q - 2) * CH + lane;
+            if (q >= L + 2) {
+                const int c = q - 2;
+                const int col = c * CH + lane;
+                int rec = INT_MIN;
                 if (col < m) {
                     // column col was written at step col + 63, in block (col + 63) / 32
                     const uint32_t v = s_out[col & 63];
@@ -445,9 +549,41 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                         of = (of <= REL_FLOOR) ? DEAD_F : of + Ou;
                     }
                     bus[col] = make_int2(oh, of);
+                    rec = oh;
+                }
+                int cmax = 0;
+                if (grow || dyn) cmax = __reduce_max_sync(FULL, rec);
+                if (grow) {
+                    grun = max(grun, cmax);
+                    if (lane == 0) grow[c] = grun;
+                }
+                // can a value of this chunk still reach the target from the next band?
+                bool useful = true;
+                if (dyn && band + 1 < pr.nbands) {
+                    const long long nrem = (long long)min(n - (band + 1) * R, m - max(0, c * CH - 2 * CH)) + 1;
+                    long long gain = (long long)P.max_sub * nrem;
+                    if (pr.gin) {
+                        const long long T = max(1LL, (long long)pr.gin_i0 - (long long)(band + 2) * R);
+                        long long k = T / pr.gin_step - 1;
+                        if (k > pr.gin_rows - 1) k = pr.gin_rows - 1;
+                        const long long r = k >= 0 ? (k + 1) * (long long)pr.gin_step : 0;
+                        const int jf = pr.gin_j0 - max(1, c * CH - 62);
+                        long long pm = 0;
+                        if (k >= 0 && jf >= 1)
+                            pm = rec_at(pr.gin + (size_t)k * (size_t)(pr.gin_nch + 2), pr.gin_nch,
+                                        min(pr.gin_nch - 1, (jf - 1) / CH));
+                        gain = min(gain, (long long)P.max_sub * ((long long)pr.gin_i0 - (long long)(band + 1) * R - r) +
+                                             P.slack + pm);
+                    }
+                    useful = (long long)cmax + gain >= (long long)target;
                 }
                 __syncwarp();
-                if (lane == 0 && band != P.fault_band) st_release(&flags[q - 2], band);
+                if (lane == 0 && band != P.fault_band) {
+                    st_release(&flags[c], 2 * band + (useful ? 1 : 0));
+                    if (dyn && useful && !first_pub) st_release(&pr.span[band].x, c);
+                }
+                if (useful) { first_pub = true; last_useful = c; }
+                last_flushed = c;
             }
             if (!anch) {
                 const int wb = __reduce_max_sync(FULL, max(best_lo, best_hi));
@@ -457,8 +593,24 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                 if (lane == 0) cancel = ld_volatile(stop) < band;
                 if (__shfl_sync(FULL, cancel, 0)) aborted = true;
             }
+            if (dyn && skip && q < nch && !aborted) {
+                // A pruned block leaves only dead state behind (lane 0 keeps the
+                // diagonal input of chunk q); the band is done when nothing useful
+                // arrives from chunk q on.  Row 0 holds nothing but the anchor.
+                int y = -1;
+                if (pred_last) {
+                    if (lane == 0) y = ld_acquire(pred_last);
+                    y = __shfl_sync(FULL, y, 0);
+                }
+                if (y != SPAN_UNPUB && q > y) break;
+            }
         }
         if (aborted) continue;
+        if (dyn && lane == 0) {
+            if (!first_pub) st_release(&pr.span[band].x, SPAN_NONE);
+            st_release(&pr.span[band].y, last_useful);
+        }
+        if (grow && lane == 0) { grow[nch] = L; grow[nch + 1] = last_flushed; }
         // band result over the 64 virtual lanes (low halves hold the smaller rows)
         int vs = best_lo, vr = rb_lo + (bk_lo < RPT ? bk_lo : 0) + 1, vc = bc_lo + 1, ok = best_lo > binit;
         {
@@ -496,34 +648,46 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
     }
 }
 
-template <int RPT, bool REL>
+template <int RPT, bool REL, bool ANCH>
 static cudaError_t launch16(const FwdParams &p, int ctas, cudaStream_t s)
 {
-    fwd16_kernel<RPT, REL><<<ctas, 128, 0, s>>>(p);
+    fwd16_kernel<RPT, REL, ANCH><<<ctas, 128, 0, s>>>(p);
     return cudaGetLastError();
+}
+
+template <int RPT>
+static cudaError_t launch16_rpt(const FwdParams &p, bool rel, bool anch, int ctas, cudaStream_t s)
+{
+    if (!rel) return anch ? cudaErrorInvalidValue : launch16<RPT, false, false>(p, ctas, s);
+    return anch ? launch16<RPT, true, true>(p, ctas, s) : launch16<RPT, true, false>(p, ctas, s);
+}
+
+template <int RPT>
+static cudaError_t occupancy16_rpt(bool rel, bool anch, int *n)
+{
+    if (!rel) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<RPT, false, false>, 128, 0);
+    return anch ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<RPT, true, true>, 128, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<RPT, true, false>, 128, 0);
 }
 
 bool fwd16_rpt_supported(int rpt) { return rpt == 4 || rpt == 8 || rpt == 16; }
 
-cudaError_t fwd16_launch(const FwdParams &p, int rpt, bool rel, int ctas, cudaStream_t s)
+cudaError_t fwd16_launch(const FwdParams &p, int rpt, bool rel, bool anch, int ctas, cudaStream_t s)
 {
     switch (rpt) {
-    case 4: return rel ? launch16<4, true>(p, ctas, s) : launch16<4, false>(p, ctas, s);
-    case 8: return rel ? launch16<8, true>(p, ctas, s) : launch16<8, false>(p, ctas, s);
-    case 16: return rel ? launch16<16, true>(p, ctas, s) : launch16<16, false>(p, ctas, s);
+    case 4: return launch16_rpt<4>(p, rel, anch, ctas, s);
+    case 8: return launch16_rpt<8>(p, rel, anch, ctas, s);
+    case 16: return launch16_rpt<16>(p, rel, anch, ctas, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t fwd16_occupancy(int rpt, bool rel, int *n)
+cudaError_t fwd16_occupancy(int rpt, bool rel, bool anch, int *n)
 {
     switch (rpt) {
-    case 4: return rel ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<4, true>, 128, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<4, false>, 128, 0);
-    case 8: return rel ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<8, true>, 128, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<8, false>, 128, 0);
-    case 16: return rel ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<16, true>, 128, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<16, false>, 128, 0);
+    case 4: return occupancy16_rpt<4>(rel, anch, n);
+    case 8: return occupancy16_rpt<8>(rel, anch, n);
+    case 16: return occupancy16_rpt<16>(rel, anch, n);
     default: return cudaErrorInvalidValue;
     }
 }

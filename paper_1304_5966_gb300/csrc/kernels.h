@@ -19,11 +19,27 @@ struct FwdProblem {          // one alignment problem, device resident
     int32_t target;          // FWD_ANCHORED: biased value sought (BIAS + S)
     int32_t transposed;      // 1: rows are the user's B (tie rule column-first)
     int2 *bus;               // m entries {H, F} of the row above the current band
-    int32_t *flags;          // ceil(m/32) entries: last band that published chunk c
+    int32_t *flags;          // ceil(m/32): 2 * (last band that released chunk c) + useful bit
+    int2 *span;              // nbands: {first, last} useful chunk of each band's bottom row
     int32_t *best;           // running best for pruning (FWD_LOCAL)
     int32_t *stop_band;      // FWD_ANCHORED: smallest band that reached the target
     int4 *band_res;          // per band {score, row(1-based), col(1-based), valid}
     int32_t *ovf;            // int16 lanes: set when a value reached the overflow guard
+    // Row record (int16x2 offset lanes only): for every band b with
+    // (b + 1) % gstride == 0, row (b + 1) / gstride - 1 of gout (gnch + 2
+    // entries) receives, per 32-column chunk q, the maximum H of the band's
+    // bottom row over columns 0 .. 32q + 31 (absolute; biased in anchored
+    // mode), then the first and last chunk written (read with rec_at).  Null:
+    // no record.
+    int32_t *gout;
+    int32_t gstride, gnch;
+    // Anchored mode: the forward pass's record of the same pair, used to bound
+    // what a path can still gain before its start (null: none).  Record row k
+    // is forward DP row (k + 1) * gin_step; this problem's DP row i and column
+    // j are forward DP row gin_i0 - i and column gin_j0 - j.
+    const int32_t *gin;
+    int32_t gin_step, gin_rows, gin_nch;
+    int32_t gin_i0, gin_j0;
 };
 
 struct FwdParams {
@@ -38,6 +54,7 @@ struct FwdParams {
     uint32_t prof_lo_t[8];   // the same for transposed problems: s(c, a)
     uint32_t prof_hi_t[8];
     int32_t go, ge, max_sub;
+    int32_t slack;           // max(go, -min_sub): what splitting a path at one cell can under-count
     int32_t prune;
     int32_t fault_band;      // testing: this band never publishes (-1 = off)
     unsigned long long timeout_ns;
@@ -48,8 +65,9 @@ bool fwd_rpt_supported(int rpt);
 // int16x2 forward kernel (local mode, alphabet <= 4): 64*rpt rows per band
 bool fwd16_rpt_supported(int rpt);
 // rel: values relative to a per-warp offset (long pairs, local and anchored modes)
-cudaError_t fwd16_launch(const FwdParams &p, int rpt, bool rel, int ctas, cudaStream_t s);
-cudaError_t fwd16_occupancy(int rpt, bool rel, int *ctas_per_sm);
+// anch: every problem of the launch is anchored (offset lanes only)
+cudaError_t fwd16_launch(const FwdParams &p, int rpt, bool rel, bool anch, int ctas, cudaStream_t s);
+cudaError_t fwd16_occupancy(int rpt, bool rel, bool anch, int *ctas_per_sm);
 cudaError_t fwd_launch(const FwdParams &p, int rpt, bool two_word_profile, int ctas,
                        int threads, cudaStream_t s);
 cudaError_t fwd_occupancy(int rpt, bool two_word_profile, int threads, int *ctas_per_sm);

@@ -82,6 +82,52 @@ __device__ __forceinline__ int2 env_band(int b, int R, int n, int m, long long a
     return make_int2(max(0, qlo), min(nch - 1, qhi));
 }
 
+// Reverse-pass record row that bounds band `band`: a path through a cell of
+// the band reaches the sink through a recorded row r at or below the band, so
+// beyond the band's frontier (its rows and the row above) it gains at most
+// max_sub per row down to r plus the largest reverse value of row r right of
+// the cell's column, plus the slack of the split cell.  gain holds the row
+// part (minus BIAS, the reverse values being biased).
+struct LabGuide { const int32_t *row; long long gain; };
+
+__device__ __forceinline__ LabGuide lab_guide(const LabProblem &pr, const LabParams &P, int band, int R)
+{
+    LabGuide g{nullptr, 0};
+    if (!(P.prune && pr.target > 0 && pr.gin) || band >= pr.nbands) return g;
+    const long long T = min((long long)pr.n, (long long)(band + 1) * R);
+    if ((long long)pr.gin_i0 - T < 0) return g;
+    long long k = ((long long)pr.gin_i0 - T) / pr.gin_step - 1;
+    if (k > pr.gin_rows - 1) k = pr.gin_rows - 1;
+    if (k < 0) return g;
+    const long long r = (long long)pr.gin_i0 - (k + 1) * (long long)pr.gin_step;
+    g.row = pr.gin + (size_t)k * (size_t)(pr.gin_nch + 2);
+    g.gain = (long long)P.max_sub * (r - (long long)band * R) + P.slack - BIAS;
+    return g;
+}
+
+// What a path can still gain, up to the sink, after a frontier node of block q
+// of `band` (every cell the block or a later block of the band computes): the
+// smaller of max_sub per remaining diagonal step less the unavoidable gap
+// columns, and the reverse-record bound.  Non-increasing in q.
+__device__ __forceinline__ long long lab_gain(const LabProblem &pr, const LabParams &P, const LabGuide &g,
+                                              int band, int q, int R)
+{
+    const long long dr_hi = (long long)pr.n - (long long)band * R, dr_lo = max(0LL, dr_hi - R);
+    const long long jlo = max(0, q * CH - CH), jhi = min(pr.m, q * CH + CH);
+    const long long dc_hi = pr.m - jlo, dc_lo = pr.m - jhi;
+    long long gapmin = 0;
+    if (dr_lo > dc_hi) gapmin = dr_lo - dc_hi;
+    if (dc_lo > dr_hi) gapmin = dc_lo - dr_hi;
+    long long gain = (long long)P.max_sub * min(dr_hi, dc_hi) - (long long)P.ge * gapmin;
+    if (g.row) {
+        // smallest column of the block's cells, as a reversed column
+        const int jr = pr.gin_j0 - max(0, q * CH - 31);
+        const int c = max(0, min(pr.gin_nch - 1, (jr - 1) / CH));
+        gain = min(gain, g.gain + rec_at(g.row, pr.gin_nch, c));
+    }
+    return gain;
+}
+
 template <int RPT, bool PREF_VERT, bool PROF2>
 __global__ void __launch_bounds__(128) lab_kernel(const LabParams P)
 {
@@ -142,7 +188,8 @@ __global__ void __launch_bounds__(128) lab_kernel(const LabParams P)
             lE[k] = LAB_INIT;
         }
         int Hlast = Hl[RPT - 1], Flast = 0, lHlast = blab, lFlast = LAB_INIT;
-        uint32_t sellast = 0;
+        // a valid selector for the cells left of the band's first column
+        uint32_t sellast = code_selector(0);
         int updiag, lupdiag;
         if (band == 0) { updiag = (lane == 0) ? BIAS : Hl[0]; lupdiag = LAB_INIT; }
         else { updiag = max(0, BIAS - border_cost(rowbase, src_f, go, ge)); lupdiag = lane ? blab : prev_blab; }
@@ -159,6 +206,8 @@ __global__ void __launch_bounds__(128) lab_kernel(const LabParams P)
 
         const int nch = (m + CH - 1) / CH;
         const int rows_left = n - band * R;
+        const bool dyn = P.prune && pr.target > 0;
+        const long long target = pr.target;
         // Static envelope: only cells whose best source-to-sink bound reaches
         // the target can lie on an optimal path, and such a cell's optimal
         // predecessors are such cells too, so chunks outside the band's range
@@ -166,10 +215,9 @@ __global__ void __launch_bounds__(128) lab_kernel(const LabParams P)
         // taken as -infinity without waiting for them.
         int q_lo = 0, q_hi = nch - 1, p_lo = 0, p_hi = nch - 1;
         {
-            const long long S = (long long)pr.target - BIAS;
+            const long long S = target - BIAS;
             const long long a_sub = P.max_sub, g_min = ge;
-            if (P.prune && pr.target > 0 &&
-                a_sub * min(n, m) - g_min * (n > m ? n - m : m - n) >= S) {
+            if (dyn && a_sub * min(n, m) - g_min * (n > m ? n - m : m - n) >= S) {
                 const int2 own = env_band(band, R, n, m, a_sub, g_min, S);
                 q_lo = own.x; q_hi = own.y;
                 if (band > 0) {
@@ -178,68 +226,116 @@ __global__ void __launch_bounds__(128) lab_kernel(const LabParams P)
                 }
             }
         }
-        if (q_lo > 0) {
-            // the band enters at chunk q_lo with everything to its left dead
+        const LabGuide gd = lab_guide(pr, P, band, R), gd_next = lab_guide(pr, P, band + 1, R);
+        const bool has_next_band = band + 1 < pr.nbands;
+        // Dynamic range: every band marks each chunk it releases as useful or
+        // not (low bit of the flag: can a value of the chunk still reach the
+        // target from the next band?) and publishes its first and last useful
+        // chunk.  The next band takes everything else as -infinity: it starts
+        // at the first useful chunk (unless the column-0 border itself can
+        // still reach the target), never waits for chunks outside the range and
+        // stops once a pruned block has nothing useful left from its column on.
+        int pfirst = 0;
+        const int *pred_last = nullptr;
+        if (dyn && band > 0) {
+            int pf = 0, ok = 1;
+            if (lane == 0) ok = wait_published(&pr.span[band - 1].x, P.err, P.timeout_ns, &pf);
+            ok = __shfl_sync(FULL, ok, 0);
+            pf = __shfl_sync(FULL, pf, 0);
+            if (!ok) continue;                // the error word is set: every band stops
+            pfirst = pf;
+            pred_last = &pr.span[band - 1].y;
+        }
+        int L = q_lo;
+        if (dyn) {
+            const long long bh = band == 0 ? BIAS : max(0, BIAS - border_cost(band * R, src_f, go, ge));
+            if (bh + lab_gain(pr, P, gd, band, 0, R) < target) L = max(L, pfirst);
+        }
+        if (L > q_hi) {
+            // nothing of this band can reach the target
+            if (lane == 0) {
+                st_release(&pr.span[band].x, SPAN_NONE);
+                st_release(&pr.span[band].y, -1);
+            }
+            continue;
+        }
+        if (L > 0) {
+            // the band enters at chunk L with everything to its left dead
 #pragma unroll
             for (int k = 0; k < RPT; ++k) { Hl[k] = 0; E[k] = 0; lHl[k] = LAB_INIT; lE[k] = LAB_INIT; }
             Hlast = 0; lHlast = LAB_INIT;
             updiag = 0; lupdiag = LAB_INIT;
         }
+        // input chunk c: 1 useful (read the bus), 0 dead, 2 not released yet
+        auto in_status = [&](int c) -> int {
+            if (c < p_lo || c > p_hi || c < pfirst) return 0;
+            const int v = ld_acquire(&flags[c]);
+            if (v >= 2 * need) return v & 1;
+            if (pred_last) {
+                const int y = ld_acquire(pred_last);
+                if (y != SPAN_UNPUB && c > y) return 0;
+            }
+            return 2;
+        };
+        // the same, waiting (bounded) for the release; -1 when the band must stop
+        auto wait_status = [&](int c) -> int {
+            int st = in_status(c);
+            if (st != 2) return st;
+            const unsigned long long t0 = globaltimer();
+            unsigned ns = 64;
+            for (;;) {
+                __nanosleep(ns);
+                if (ns < 256) ns <<= 1;
+                st = in_status(c);
+                if (st != 2) return st;
+                if (ld_volatile(P.err)) return -1;
+                if (globaltimer() - t0 > P.timeout_ns) { atomicCAS(P.err, 0, DEV_ETIMEOUT); return -1; }
+            }
+        };
         {
-            const bool live_in = q_lo >= p_lo && q_lo <= p_hi;
-            int ok = 1;
-            if (lane == 0 && live_in) ok = wait_flag(&flags[q_lo], need, P.err, nullptr, 0, P.timeout_ns);
-            ok = __shfl_sync(FULL, ok, 0);
-            if (!ok) aborted = true;
+            int st = 0;
+            if (lane == 0) st = wait_status(L);
+            st = __shfl_sync(FULL, st, 0);
+            if (st < 0) aborted = true;
             else {
                 int4 v = make_int4(0, 0, LAB_INIT, LAB_INIT);
                 uint32_t sel = 0;
-                const int col = q_lo * CH + lane;
+                const int col = L * CH + lane;
                 if (col < m) {
-                    if (live_in) v = bus[col];
+                    if (st == 1) v = bus[col];
                     sel = code_selector(bseq[col]);
                 }
-                s_in[q_lo & 1][lane] = v;
-                s_sel[q_lo & 1][lane] = sel;
+                s_in[L & 1][lane] = v;
+                s_sel[L & 1][lane] = sel;
             }
             __syncwarp();
         }
-        for (int q = q_lo; q <= q_hi + 1 && !aborted; ++q) {
+        bool first_pub = false;
+        int last_useful = -1;
+        for (int q = L; q <= q_hi + 1 && !aborted; ++q) {
             const int buf = q & 1;
             const bool has_next = q + 1 <= q_hi;
-            const bool next_live = q + 1 >= p_lo && q + 1 <= p_hi;
-            int ready = 0;
+            int nst = 0;
             int4 nv = make_int4(0, 0, LAB_INIT, LAB_INIT);
             uint32_t nsel = 0;
             const int ncol = (q + 1) * CH + lane;
             if (has_next) {
-                ready = 1;
-                if (next_live) {
-                    if (lane == 0) ready = ld_acquire(&flags[q + 1]) >= need;
-                    ready = __shfl_sync(FULL, ready, 0);
-                }
-                if (ready && ncol < m) {
-                    if (next_live) nv = bus[ncol];
+                if (lane == 0) nst = in_status(q + 1);
+                nst = __shfl_sync(FULL, nst, 0);
+                if (nst != 2 && ncol < m) {
+                    if (nst == 1) nv = bus[ncol];
                     nsel = code_selector(bseq[ncol]);
                 }
             }
             bool skip = false;
-            if (P.prune && pr.target > 0) {
+            if (dyn) {
                 int mx = 0;
 #pragma unroll
                 for (int k = 0; k < RPT; ++k) mx = max(mx, Hl[k]);
                 mx = max(mx, max(Hlast, updiag));
                 if (q <= q_hi) mx = max(mx, s_in[buf][lane].x);
                 mx = __reduce_max_sync(FULL, mx);
-                // rows / columns still to go from any node this block touches
-                const long long dr_hi = (long long)n - band * R, dr_lo = max(0LL, dr_hi - R);
-                const long long jlo = max(0, q * CH - CH), jhi = min(m, q * CH + CH);
-                const long long dc_hi = m - jlo, dc_lo = m - jhi;
-                long long gapmin = 0;
-                if (dr_lo > dc_hi) gapmin = dr_lo - dc_hi;
-                if (dc_lo > dr_hi) gapmin = dc_lo - dr_hi;
-                const long long gain = (long long)P.max_sub * min(dr_hi, dc_hi) - (long long)ge * gapmin;
-                skip = (long long)mx + gain < (long long)pr.target;
+                skip = (long long)mx + lab_gain(pr, P, gd, band, q, R) < target;
             }
             ++tiles;
             if (skip) {
@@ -324,33 +420,66 @@ __global__ void __launch_bounds__(128) lab_kernel(const LabParams P)
                 }
             }
             if (has_next) {
-                if (!ready) {
-                    int ok = 1;
-                    if (lane == 0) ok = wait_flag(&flags[q + 1], need, P.err, nullptr, 0, P.timeout_ns);
-                    ok = __shfl_sync(FULL, ok, 0);
-                    if (!ok) { aborted = true; break; }
-                    if (ncol < m) { nv = bus[ncol]; nsel = code_selector(bseq[ncol]); }
+                if (nst == 2) {
+                    int st = 0;
+                    if (lane == 0) st = wait_status(q + 1);
+                    st = __shfl_sync(FULL, st, 0);
+                    if (st < 0) { aborted = true; break; }
+                    if (ncol < m) {
+                        if (st == 1) nv = bus[ncol];
+                        nsel = code_selector(bseq[ncol]);
+                    }
                 }
                 s_in[buf ^ 1][lane] = nv;
                 s_sel[buf ^ 1][lane] = nsel;
             }
             __syncwarp();
-            if (q > q_lo) {
-                const int col = (q - 1) * CH + lane;
+            if (q > L) {
+                const int c = q - 1;
+                const int col = c * CH + lane;
+                int hmax = 0;
                 if (col < m) {
                     const int4 o = s_out[col & 63];
                     bus[col] = o;
                     if (ck_row) ck_row[col] = o;
+                    hmax = o.x;
+                }
+                bool useful = true;
+                if (dyn && has_next_band) {
+                    hmax = __reduce_max_sync(FULL, hmax);
+                    useful = (long long)hmax + lab_gain(pr, P, gd_next, band + 1, c, R) >= target;
                 }
                 __syncwarp();
-                if (lane == 0) st_release(&flags[q - 1], band);
+                if (lane == 0) {
+                    st_release(&flags[c], 2 * band + (useful ? 1 : 0));
+                    if (useful && dyn && !first_pub) st_release(&pr.span[band].x, c);
+                }
+                if (useful) { first_pub = true; last_useful = c; }
+            }
+            if (dyn && skip && q <= q_hi) {
+                // a pruned block leaves only dead state behind; the band is done
+                // when nothing useful arrives from chunk q on
+                int done = q > p_hi;
+                if (!done && pred_last) {
+                    int y = SPAN_UNPUB;
+                    if (lane == 0) y = ld_acquire(pred_last);
+                    y = __shfl_sync(FULL, y, 0);
+                    done = y != SPAN_UNPUB && q > y;
+                }
+                if (done) break;
             }
         }
-        if (!aborted && lane == 0) {
-            atomicAdd(&P.stats[1], (unsigned long long)tiles);
-            atomicAdd(&P.stats[2], (unsigned long long)pruned);
-            atomicAdd(&P.stats[0], (unsigned long long)(tiles - pruned) * CH *
-                                       (unsigned long long)min(R, rows_left));
+        if (!aborted) {
+            if (dyn && lane == 0) {
+                if (!first_pub) st_release(&pr.span[band].x, SPAN_NONE);
+                st_release(&pr.span[band].y, last_useful);
+            }
+            if (lane == 0) {
+                atomicAdd(&P.stats[1], (unsigned long long)tiles);
+                atomicAdd(&P.stats[2], (unsigned long long)pruned);
+                atomicAdd(&P.stats[0], (unsigned long long)(tiles - pruned) * CH *
+                                           (unsigned long long)min(R, rows_left));
+            }
         }
     }
 }
@@ -368,7 +497,8 @@ __global__ void lab_init_kernel(LabProblem *probs, int nprobs, int go, int ge)
         pr.bus[j] = make_int4(max(0, BIAS - c), 0, LAB_INIT, LAB_INIT);
     }
     const int nch = (pr.m + CH - 1) / CH;
-    for (int c = threadIdx.x; c < nch; c += blockDim.x) pr.flags[c] = -1;
+    for (int c = threadIdx.x; c < nch; c += blockDim.x) pr.flags[c] = -1;   // row 0: released, useful
+    for (int b = threadIdx.x; b < pr.nbands; b += blockDim.x) pr.span[b] = make_int2(SPAN_UNPUB, SPAN_UNPUB);
     if (threadIdx.x == 0) {
         pr.sink[0] = make_int4(0, 0, 0, 0);
         pr.sink[1] = make_int4(0, 0, 0, 0);

@@ -21,9 +21,17 @@ struct LabProblem {
     int32_t ck;            // bands per checkpoint (0: none)
     int32_t target;        // biased optimum at the sink (BIAS + S) or 0 when unknown
     int4 *bus;             // m x {H, F, labH, labF}
-    int32_t *flags;        // ceil(m/32)
+    int32_t *flags;        // ceil(m/32): 2 * (last band that released the chunk) + useful bit
+    int2 *span;            // nbands: {first, last} useful chunk of each band's bottom row
     int4 *ckpt;            // nck x m x {H, F, labH, labF}
     int4 *sink;            // [0] {H, F, E, done}  [1] {labH, labF, labE, done}
+    // Row record of the reverse anchored pass from this problem's sink (null:
+    // none): row k holds, per 32-column chunk c of the reversed matrix, the
+    // largest biased H of reversed columns 0 .. 32c + 31 on reversed row
+    // (k + 1) * gin_step, which is this problem's row gin_i0 - (k + 1) * gin_step;
+    // this problem's column j is reversed column gin_j0 - j.
+    const int32_t *gin;
+    int32_t gin_step, gin_rows, gin_nch, gin_i0, gin_j0;
 };
 
 struct LabParams {
@@ -35,6 +43,7 @@ struct LabParams {
     unsigned long long *stats;
     uint32_t prof_lo[8], prof_hi[8];
     int32_t go, ge, max_sub;
+    int32_t slack;         // max(go, -min_sub)
     int32_t prune;
     unsigned long long timeout_ns;
 };
