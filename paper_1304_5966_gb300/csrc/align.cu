@@ -455,6 +455,10 @@ int find_start(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const uint8_
     if (prune) {
         jobs[0].gout = rev_rec;
         jobs[0].gin = fwd_rec;
+        // Bounded by the forward record, the pass follows a narrow band around
+        // the path; its bands form a chain whose length is the band height
+        // times the rows per thread, so thin lanes finish first.
+        if (fwd_rec && fwd_rec->valid) jobs[0].rpt16 = 4;
         jobs[0].gin_i0 = (int32_t)(a_end + 1);
         jobs[0].gin_j0 = (int32_t)(b_end + 1);
     }

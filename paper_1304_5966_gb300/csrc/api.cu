@@ -300,7 +300,8 @@ int run_forward(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &job
                         (ctx->opt.forward_lanes == 16 || rpt <= 0);
     if (!rel_ok) return run_forward32(ctx, sc, jobs, prune, rpt, res, stats, ms);
     std::vector<int> ovf;
-    const int rpt16 = (ctx->opt.forward_lanes == 16 && fwd16_rpt_supported(rpt) && rel16_fits(sc, rpt)) ? rpt : 0;
+    int rpt16 = (ctx->opt.forward_lanes == 16 && fwd16_rpt_supported(rpt) && rel16_fits(sc, rpt)) ? rpt : 0;
+    if (rpt16 == 0 && fwd16_rpt_supported(jobs[0].rpt16) && rel16_fits(sc, jobs[0].rpt16)) rpt16 = jobs[0].rpt16;
     int st = run_forward_impl(ctx, sc, jobs, prune, rpt16, true, true, res, &ovf, stats, ms);
     if (st) return st;
     std::vector<FwdJob> redo;

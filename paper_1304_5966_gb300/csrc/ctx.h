@@ -155,6 +155,7 @@ struct FwdJob {
     int32_t mode;          // FwdMode
     int32_t target;        // anchored: biased target
     int32_t transposed;
+    int32_t rpt16 = 0;             // rows per thread on int16x2 lanes (0: chosen by size)
     Guide *gout = nullptr;         // record this pass's rows here
     const Guide *gin = nullptr;    // anchored: forward record to prune with
     int32_t gin_i0 = 0, gin_j0 = 0;

@@ -67,11 +67,61 @@ __device__ __forceinline__ int to_rel(int v, int O, bool anch)
     return (int)(r < REL_FLOOR ? REL_FLOOR : (r > 32767 ? 32767 : r));
 }
 
+// Anchored with the forward record: any path through a cell of band `band`
+// that reaches the start crosses a recorded forward row r at or above the band
+// (or starts below it), so what it gains beyond the band's frontier (its rows
+// and the row above) is at most max_sub per row from the frontier up to r, plus
+// the largest forward H of row r left of the cell's column, plus the slack of
+// the split cell.  Row 0 of the forward matrix is all zero.
+struct GinRow {
+    const int32_t *row = nullptr;
+    long long gain = 0;            // max_sub * rows + slack (add the record entry)
+    int lo = 1, hi = 0, nch = 0;   // written chunk range of the row
+    bool valid = false;
+    // record entry bounding forward columns up to jf (0 below the written range)
+    __device__ __forceinline__ int at(int jf) const {
+        if (!row || jf < 1) return 0;
+        const int c = min(nch - 1, (jf - 1) / CH);
+        if (hi < lo || c < lo) return 0;
+        return row[min(c, hi)];
+    }
+};
+
+__device__ __forceinline__ GinRow gin_for_band(const FwdProblem &pr, const FwdParams &P, int band, int R)
+{
+    GinRow g;
+    if (!pr.gin) return g;
+    const long long T = max(1LL, (long long)pr.gin_i0 - (long long)(band + 1) * R);
+    long long k = T / pr.gin_step - 1;
+    if (k > pr.gin_rows - 1) k = pr.gin_rows - 1;
+    const long long r = k >= 0 ? (k + 1) * (long long)pr.gin_step : 0;
+    if (k >= 0) {
+        g.row = pr.gin + (size_t)k * (size_t)(pr.gin_nch + 2);
+        g.nch = pr.gin_nch;
+        g.lo = g.row[pr.gin_nch];
+        g.hi = g.row[pr.gin_nch + 1];
+    }
+    g.gain = (long long)P.max_sub * ((long long)pr.gin_i0 - (long long)band * R - r) + P.slack;
+    g.valid = true;
+    return g;
+}
+
 template <int RPT, bool REL, bool ANCH>
 __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
 {
     __shared__ int4 s_in_all[4][3][CH];   // {H, F, selector8, 0} per column, three chunks
     __shared__ uint32_t s_out_all[4][2 * CH];   // bottom row, packed int16 (H | F << 16)
+    // Grouped launch (anchored): a CTA takes four consecutive tickets, and a band
+    // whose successor runs in the same CTA hands its bottom row over through a
+    // ring of GK chunks in shared memory instead of the boundary row in HBM.
+    // The anchored pass follows a narrow band around the path, where the bands
+    // form a chain and the hand-over latency is the pass's time.
+    constexpr bool GROUP = ANCH;
+    constexpr int GW = 4, GK = 8;
+    __shared__ int2 s_ring[GROUP ? GW : 1][GROUP ? GK : 1][CH];   // absolute {H, F}
+    __shared__ int s_tag[GROUP ? GW : 1][GROUP ? GK : 1];         // 2 * chunk + useful
+    __shared__ int s_need[GW], s_spx[GW], s_spy[GW];              // reader's next chunk; span
+    __shared__ int s_base, s_err;
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     int4 (*s_in)[CH] = s_in_all[wid];
@@ -85,11 +135,25 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
     constexpr int R = 64 * RPT;
 
     for (;;) {
-        int tk = 0, stop_now = 0;
-        if (lane == 0) { tk = atomicAdd(P.ticket_ctr, 1); stop_now = ld_volatile(P.err); }
-        tk = __shfl_sync(FULL, tk, 0);
-        stop_now = __shfl_sync(FULL, stop_now, 0);
-        if (tk >= P.ntickets || stop_now) return;
+        int tk = 0, stop_now = 0, gbase = 0;
+        if (GROUP) {
+            __syncthreads();                               // the previous group is done
+            if (threadIdx.x == 0) { s_base = atomicAdd(P.ticket_ctr, GW); s_err = ld_volatile(P.err); }
+            if (lane == 0) {
+                for (int k = 0; k < GK; ++k) s_tag[wid][k] = -1;
+                s_need[wid] = INT_MIN; s_spx[wid] = SPAN_UNPUB; s_spy[wid] = SPAN_UNPUB;
+            }
+            __syncthreads();
+            gbase = s_base;
+            if (gbase >= P.ntickets || s_err) return;      // the whole CTA leaves together
+            tk = gbase + wid;
+            if (tk >= P.ntickets) continue;
+        } else {
+            if (lane == 0) { tk = atomicAdd(P.ticket_ctr, 1); stop_now = ld_volatile(P.err); }
+            tk = __shfl_sync(FULL, tk, 0);
+            stop_now = __shfl_sync(FULL, stop_now, 0);
+            if (tk >= P.ntickets || stop_now) return;
+        }
         const int2 tb = P.tickets[tk];
         const FwdProblem &pr = P.probs[tb.x];
         const int band = tb.y;
@@ -128,29 +192,63 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
         // takes everything else as minus infinity without waiting for it and
         // stops once a pruned block has nothing useful left from its column on.
         const bool dyn = anch && P.prune;
+        // neighbours in this CTA's group: the predecessor's row arrives through
+        // its ring, this band's row leaves through its own ring
+        const bool pred_in = GROUP && wid > 0 && P.tickets[tk - 1].x == tb.x && P.tickets[tk - 1].y == band - 1;
+        const bool succ_in = GROUP && wid < GW - 1 && tk + 1 < P.ntickets && P.tickets[tk + 1].x == tb.x &&
+                             P.tickets[tk + 1].y == band + 1;
+        volatile int *vtag = GROUP && pred_in ? (volatile int *)s_tag[wid - 1] : nullptr;
+        volatile int *vneed = (volatile int *)s_need;
+        volatile int *vspx = (volatile int *)s_spx, *vspy = (volatile int *)s_spy;
+        // the reader of this band's ring no longer needs anything (bands that end early)
+        auto release_reader = [&]() {
+            if (GROUP && lane == 0) { __threadfence_block(); vneed[wid] = INT_MAX; }
+        };
         int pfirst = 0;
         const int *pred_last = nullptr;
         if (dyn && band > 0) {
             int pf = 0, ok = 1;
-            if (lane == 0) ok = wait_published(&pr.span[band - 1].x, P.err, P.timeout_ns, &pf, stop, band);
+            if (lane == 0) {
+                if (pred_in) {
+                    const unsigned long long t0 = globaltimer();
+                    for (;;) {
+                        pf = vspx[wid - 1];
+                        if (pf != SPAN_UNPUB) break;
+                        __nanosleep(20);
+                        if (ld_volatile(P.err) || (stop && ld_volatile(stop) < band)) { ok = 0; break; }
+                        if (globaltimer() - t0 > P.timeout_ns) { atomicCAS(P.err, 0, DEV_ETIMEOUT); ok = 0; break; }
+                    }
+                    __threadfence_block();
+                } else {
+                    ok = wait_published(&pr.span[band - 1].x, P.err, P.timeout_ns, &pf, stop, band);
+                }
+            }
             ok = __shfl_sync(FULL, ok, 0);
             pf = __shfl_sync(FULL, pf, 0);
-            if (!ok) continue;                // error, or the search already ended above
+            if (!ok) { release_reader(); continue; }    // error, or the search already ended above
             pfirst = pf;
-            pred_last = &pr.span[band - 1].y;
+            pred_last = pred_in ? nullptr : &pr.span[band - 1].y;
         }
         const int L = pfirst;
         if (L >= nch) {
             // nothing from above can reach the target: neither can this band
             if (lane == 0) {
-                st_release(&pr.span[band].x, SPAN_NONE);
-                st_release(&pr.span[band].y, -1);
+                if (succ_in) { vspx[wid] = SPAN_NONE; vspy[wid] = -1; }
+                else { st_release(&pr.span[band].x, SPAN_NONE); st_release(&pr.span[band].y, -1); }
             }
+            release_reader();
             continue;
         }
-        // input chunk c: 1 useful (read the bus), 0 dead, 2 not released yet
+        // input chunk c: 1 useful (read it), 0 dead, 2 not released yet
         auto in_status = [&](int c) -> int {
             if (c < pfirst) return 0;
+            if (pred_in) {
+                const int t = vtag[c % GK];
+                if ((t >> 1) == c) { __threadfence_block(); return t & 1; }
+                const int y = vspy[wid - 1];
+                if (y != SPAN_UNPUB && c > y) return 0;
+                return 2;
+            }
             const int v = ld_acquire(&flags[c]);
             if (v >= 2 * need) return v & 1;
             if (pred_last) {
@@ -159,6 +257,19 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
             }
             return 2;
         };
+        // one column of input chunk c (st = 1: released and useful); ring reads
+        // follow a __syncwarp after the status broadcast, which orders them
+        // after lane 0's view of the tag
+        auto in_load = [&](int c, int col) -> int2 {
+            return pred_in ? s_ring[GROUP ? wid - 1 : 0][GROUP ? c % GK : 0][lane] : bus[col];
+        };
+        // tell the predecessor that chunks before `next` have been read
+        auto mark_read = [&](int next) {
+            if (GROUP && pred_in) {
+                __syncwarp();
+                if (lane == 0) { __threadfence_block(); vneed[wid] = next; }
+            }
+        };
         // the same, waiting (bounded) for the release; -1 when the band must stop
         auto wait_status = [&](int c) -> int {
             int st = in_status(c);
@@ -166,8 +277,12 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
             const unsigned long long t0 = globaltimer();
             unsigned ns = 64;
             for (;;) {
-                __nanosleep(ns);
-                if (ns < 256) ns <<= 1;
+                if (!pred_in) {
+                    __nanosleep(ns);
+                    if (ns < 256) ns <<= 1;
+                } else {
+                    __nanosleep(20);
+                }
                 st = in_status(c);
                 if (st != 2) return st;
                 if (ld_volatile(P.err)) return -1;
@@ -184,15 +299,17 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                 int2 v = make_int2(DEAD_H, DEAD_F);
                 uint32_t sel = 0;
                 const int col = L * CH + lane;
+                if (pred_in) __syncwarp();
                 if (col < m) {
-                    if (st == 1) v = bus[col];
+                    if (st == 1) v = in_load(L, col);
                     sel = sel_lo8(bseq[col]);
                 }
                 s_in[L % 3][lane] = make_int4(v.x, v.y, (int)sel, 0);
             }
+            mark_read(L + 1);
             __syncwarp();
         }
-        if (aborted) continue;
+        if (aborted) { release_reader(); continue; }
         // ---- offset, floor and initial state
         int O = 0;
         uint32_t fl2 = ZERO2;                              // the local zero floor (relative)
@@ -229,7 +346,15 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
             const long long t = (long long)max(b, binit + 1) - O;
             return (int)(t > 32767 ? 32767 : (t < -32768 ? -32768 : t));
         };
-        uint32_t thr = REL ? p16(thr_of(best_lo), thr_of(best_hi)) : p16(1, 1);
+        // Detection threshold minus one per half (saturating): a step whose
+        // running maximum exceeds it may hold a new best, ties included.  The
+        // test is a per-half max and one compare; the DPX max-with-predicates
+        // form produced missed maxima in this kernel under ptxas -O2 and above.
+        auto thr_minus1 = [&](int bl, int bh) -> uint32_t {
+            const int tl = REL ? thr_of(bl) : max(bl, 1), th = REL ? thr_of(bh) : max(bh, 1);
+            return p16(max(tl - 1, -32768), max(th - 1, -32768));
+        };
+        uint32_t thr1 = thr_minus1(best_lo, best_hi);
         int published = 0;
         unsigned tiles = 0, pruned = 0;
         // row record of this band's bottom row (running maximum over chunks)
@@ -242,24 +367,25 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
         // is at most max_sub per row from the frontier up to r, plus the largest
         // forward H of row r left of the cell's column (plus the slack of the
         // split cell).  Row 0 of the forward matrix is all zero.
-        const int32_t *gin_row = nullptr;
-        long long gin_gain = 0;
-        if (anch && pr.gin) {
-            const long long T = max(1LL, (long long)pr.gin_i0 - (long long)(band + 1) * R);
-            long long k = T / pr.gin_step - 1;
-            if (k > pr.gin_rows - 1) k = pr.gin_rows - 1;
-            const long long r = k >= 0 ? (k + 1) * (long long)pr.gin_step : 0;
-            if (k >= 0) gin_row = pr.gin + (size_t)k * (size_t)(pr.gin_nch + 2);
-            gin_gain = (long long)P.max_sub * ((long long)pr.gin_i0 - (long long)band * R - r) + P.slack;
-        }
+        // The same bound for the next band decides which output chunks are
+        // useful to it.  Both record rows' written ranges are read once.
+        const GinRow gin_own = anch ? gin_for_band(pr, P, band, R) : GinRow{};
+        const GinRow gin_nx = (anch && dyn && band + 1 < pr.nbands) ? gin_for_band(pr, P, band + 1, R) : GinRow{};
         unsigned long long cells = 0;
         const int rows_lo = max(0, min(RPT, n - rb_lo)), rows_hi = max(0, min(RPT, n - rb_hi));
         int O_even = O, O_odd = O;                         // offset used in each block (by parity)
 
         bool first_pub = false;
-        int last_useful = -1, last_flushed = -1;
+        int last_useful = -1, last_flushed = -1, ring_first = 0;
         for (int q = L; q < nblk && !aborted; ++q) {
             const int buf = q % 3;
+            // loads whose results are needed only later in the block, issued first
+            // so that their latency overlaps the flag probe and the block's work:
+            // the record entries for this block and for the chunk flushed at its
+            // end, and the word that ends the search
+            const int pm_own = gin_own.at(pr.gin_j0 - max(1, q * CH - 62));
+            const int pm_nx = gin_nx.at(pr.gin_j0 - max(1, (q - 2) * CH - 62));
+            const int stop_seen = (anch && stop && lane == 0) ? ld_volatile(stop) : INT_MAX;
             const bool has_next = (q + 1) < nch;
             int nst = 0;
             int2 nv = make_int2(DEAD_H, DEAD_F);
@@ -268,9 +394,13 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
             if (has_next) {
                 if (lane == 0) nst = in_status(q + 1);
                 nst = __shfl_sync(FULL, nst, 0);
-                if (nst != 2 && ncol < m) {
-                    if (nst == 1) nv = bus[ncol];
-                    nsel = sel_lo8(bseq[ncol]);
+                if (nst != 2) {
+                    if (pred_in) __syncwarp();
+                    if (ncol < m) {
+                        if (nst == 1) nv = in_load(q + 1, ncol);
+                        nsel = sel_lo8(bseq[ncol]);
+                    }
+                    mark_read(q + 2);
                 }
             }
             // ---- relative mode: re-centre the offset on the window's largest value
@@ -319,7 +449,7 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                     }
                     const int z = anch ? REL_FLOOR : to_rel(0, O, false);
                     fl2 = p16(z, z);
-                    thr = p16(thr_of(best_lo), thr_of(best_hi));
+                    thr1 = thr_minus1(best_lo, best_hi);
                 }
                 if (q < nch) {
                     const int4 c = s_in[buf][lane];
@@ -347,14 +477,8 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                 const int jmin = max(0, q * CH - 2 * CH);
                 const long long rem = (long long)min(rows_left, m - jmin) + 1;
                 skip = mxa + (long long)P.max_sub * rem < (long long)pthr;
-                if (!skip && anch && pr.gin) {
-                    // largest forward column of the block's cells, and the record
-                    // of row r up to it
-                    const int jf = pr.gin_j0 - max(1, q * CH - 62);
-                    long long pm = 0;
-                    if (gin_row && jf >= 1) pm = rec_at(gin_row, pr.gin_nch, min(pr.gin_nch - 1, (jf - 1) / CH));
-                    skip = mxa + gin_gain + pm < (long long)pthr;
-                }
+                if (!skip && gin_own.valid)
+                    skip = mxa + gin_own.gain + pm_own < (long long)pthr;
             }
             ++tiles;
             const bool ramp = (q * CH < 2 * CH) || (q * CH + CH - 1 >= m);
@@ -411,9 +535,8 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                     }
                     Hlast = Hl[RPT - 1];
                     Flast = F;
-                    bool ph, pl;
-                    __vibmax_s16x2(smax, thr, &ph, &pl);
-                    if (ph || pl) {
+                    if (vmax16(smax, thr1) != thr1) {
+                        const bool pl = lo16(smax) > lo16(thr1), ph = hi16(smax) > hi16(thr1);
                         const int jlo = s - lane, jhi = s - lane - 32;
                         const int sl = lo16(smax) + O, sh = hi16(smax) + O;
                         if (pl) {
@@ -428,7 +551,7 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                             for (int k = RPT - 1; k >= 0; --k) if (hi16(Hl[k]) + O == sh) kf = k;
                             if (sh > best_hi || (!transposed && kf < bk_hi)) { best_hi = sh; bk_hi = kf; bc_hi = jhi; }
                         }
-                        thr = REL ? p16(thr_of(best_lo), thr_of(best_hi)) : p16(max(best_lo, 1), max(best_hi, 1));
+                        thr1 = thr_minus1(best_lo, best_hi);
                         if (!REL && max(best_lo, best_hi) >= guard && pr.ovf) atomicExch(pr.ovf, 1);
                     }
                     if (lane == 31) s_out[(s - 63) & 63] = perm(Hlast, Flast, 0x7632u);
@@ -497,9 +620,8 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                             Hlast = Hl[RPT - 1];
                             Flast = perm(F, oFlast, ks);
                         }
-                        bool ph, pl;
-                        __vibmax_s16x2(smax, thr, &ph, &pl);
-                        if (ph || pl) {
+                        if (vmax16(smax, thr1) != thr1) {
+                            const bool pl = lo16(smax) > lo16(thr1), ph = hi16(smax) > hi16(thr1);
                             const int sl = lo16(smax) + O, sh = hi16(smax) + O;
                             if (pl && vlo) {
                                 int kf = RPT;
@@ -513,7 +635,7 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                                 for (int k = RPT - 1; k >= 0; --k) if (hi16(Hl[k]) + O == sh) kf = k;
                                 if (sh > best_hi || (!transposed && kf < bk_hi)) { best_hi = sh; bk_hi = kf; bc_hi = jhi; }
                             }
-                            thr = REL ? p16(thr_of(best_lo), thr_of(best_hi)) : p16(max(best_lo, 1), max(best_hi, 1));
+                            thr1 = thr_minus1(best_lo, best_hi);
                             if (!REL && max(best_lo, best_hi) >= guard && pr.ovf) atomicExch(pr.ovf, 1);
                         }
                         if (lane == 31 && vhi) s_out[jhi & 63] = perm(Hlast, Flast, 0x7632u);
@@ -527,10 +649,12 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                     if (lane == 0) st = wait_status(q + 1);
                     st = __shfl_sync(FULL, st, 0);
                     if (st < 0) { aborted = true; break; }
+                    if (pred_in) __syncwarp();
                     if (ncol < m) {
-                        if (st == 1) nv = bus[ncol];
+                        if (st == 1) nv = in_load(q + 1, ncol);
                         nsel = sel_lo8(bseq[ncol]);
                     }
+                    mark_read(q + 2);
                 }
                 s_in[(q + 1) % 3][lane] = make_int4(nv.x, nv.y, (int)nsel, 0);
             }
@@ -539,6 +663,7 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                 const int c = q - 2;
                 const int col = c * CH + lane;
                 int rec = INT_MIN;
+                int2 outv = make_int2(DEAD_H, DEAD_F);
                 if (col < m) {
                     // column col was written at step col + 63, in block (col + 63) / 32
                     const uint32_t v = s_out[col & 63];
@@ -548,7 +673,8 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                         oh = (oh <= REL_FLOOR) ? DEAD_H : oh + Ou;
                         of = (of <= REL_FLOOR) ? DEAD_F : of + Ou;
                     }
-                    bus[col] = make_int2(oh, of);
+                    outv = make_int2(oh, of);
+                    if (!succ_in) bus[col] = outv;
                     rec = oh;
                 }
                 int cmax = 0;
@@ -562,25 +688,41 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                 if (dyn && band + 1 < pr.nbands) {
                     const long long nrem = (long long)min(n - (band + 1) * R, m - max(0, c * CH - 2 * CH)) + 1;
                     long long gain = (long long)P.max_sub * nrem;
-                    if (pr.gin) {
-                        const long long T = max(1LL, (long long)pr.gin_i0 - (long long)(band + 2) * R);
-                        long long k = T / pr.gin_step - 1;
-                        if (k > pr.gin_rows - 1) k = pr.gin_rows - 1;
-                        const long long r = k >= 0 ? (k + 1) * (long long)pr.gin_step : 0;
-                        const int jf = pr.gin_j0 - max(1, c * CH - 62);
-                        long long pm = 0;
-                        if (k >= 0 && jf >= 1)
-                            pm = rec_at(pr.gin + (size_t)k * (size_t)(pr.gin_nch + 2), pr.gin_nch,
-                                        min(pr.gin_nch - 1, (jf - 1) / CH));
-                        gain = min(gain, (long long)P.max_sub * ((long long)pr.gin_i0 - (long long)(band + 1) * R - r) +
-                                             P.slack + pm);
-                    }
+                    if (gin_nx.valid) gain = min(gain, gin_nx.gain + pm_nx);
                     useful = (long long)cmax + gain >= (long long)target;
                 }
-                __syncwarp();
-                if (lane == 0 && band != P.fault_band) {
-                    st_release(&flags[c], 2 * band + (useful ? 1 : 0));
-                    if (dyn && useful && !first_pub) st_release(&pr.span[band].x, c);
+                if (succ_in) {
+                    // The ring carries chunks from the first useful one on (the
+                    // reader starts there); a slot is reused once the reader has
+                    // moved GK chunks past it.
+                    if (first_pub || useful) {
+                        if (!first_pub) ring_first = c;
+                        int ok = 1;
+                        // slot c % GK last held chunk c - GK: wait until the reader is past it
+                        if (lane == 0 && c - GK >= ring_first && c - GK >= vneed[wid + 1]) {
+                            const unsigned long long t0 = globaltimer();
+                            while (c - GK >= vneed[wid + 1]) {
+                                __nanosleep(20);
+                                if (ld_volatile(P.err)) { ok = 0; break; }
+                                if (globaltimer() - t0 > P.timeout_ns) { atomicCAS(P.err, 0, DEV_ETIMEOUT); ok = 0; break; }
+                            }
+                            __threadfence_block();
+                        }
+                        if (!__shfl_sync(FULL, ok, 0)) { aborted = true; break; }
+                        s_ring[GROUP ? wid : 0][GROUP ? c % GK : 0][lane] = outv;
+                        __syncwarp();
+                        if (lane == 0) {
+                            __threadfence_block();
+                            ((volatile int *)s_tag[GROUP ? wid : 0])[GROUP ? c % GK : 0] = 2 * c + (useful ? 1 : 0);
+                            if (dyn && useful && !first_pub) vspx[wid] = c;
+                        }
+                    }
+                } else {
+                    __syncwarp();
+                    if (lane == 0 && band != P.fault_band) {
+                        st_release(&flags[c], 2 * band + (useful ? 1 : 0));
+                        if (dyn && useful && !first_pub) st_release(&pr.span[band].x, c);
+                    }
                 }
                 if (useful) { first_pub = true; last_useful = c; }
                 last_flushed = c;
@@ -589,26 +731,31 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                 const int wb = __reduce_max_sync(FULL, max(best_lo, best_hi));
                 if (lane == 0 && wb > published) { atomicMax(pr.best, wb); published = wb; }
             } else if (stop != nullptr) {
-                int cancel = 0;
-                if (lane == 0) cancel = ld_volatile(stop) < band;
-                if (__shfl_sync(FULL, cancel, 0)) aborted = true;
+                if (__shfl_sync(FULL, stop_seen < band ? 1 : 0, 0)) aborted = true;
             }
             if (dyn && skip && q < nch && !aborted) {
                 // A pruned block leaves only dead state behind (lane 0 keeps the
                 // diagonal input of chunk q); the band is done when nothing useful
                 // arrives from chunk q on.  Row 0 holds nothing but the anchor.
                 int y = -1;
-                if (pred_last) {
-                    if (lane == 0) y = ld_acquire(pred_last);
+                if (pred_in || pred_last) {
+                    if (lane == 0) y = pred_in ? vspy[wid - 1] : ld_acquire(pred_last);
                     y = __shfl_sync(FULL, y, 0);
                 }
                 if (y != SPAN_UNPUB && q > y) break;
             }
         }
+        release_reader();
         if (aborted) continue;
         if (dyn && lane == 0) {
-            if (!first_pub) st_release(&pr.span[band].x, SPAN_NONE);
-            st_release(&pr.span[band].y, last_useful);
+            if (succ_in) {
+                __threadfence_block();
+                if (!first_pub) vspx[wid] = SPAN_NONE;
+                vspy[wid] = last_useful;
+            } else {
+                if (!first_pub) st_release(&pr.span[band].x, SPAN_NONE);
+                st_release(&pr.span[band].y, last_useful);
+            }
         }
         if (grow && lane == 0) { grow[nch] = L; grow[nch + 1] = last_flushed; }
         // band result over the 64 virtual lanes (low halves hold the smaller rows)

@@ -88,11 +88,24 @@ __device__ __forceinline__ int2 env_band(int b, int R, int n, int m, long long a
 // max_sub per row down to r plus the largest reverse value of row r right of
 // the cell's column, plus the slack of the split cell.  gain holds the row
 // part (minus BIAS, the reverse values being biased).
-struct LabGuide { const int32_t *row; long long gain; };
+struct LabGuide {
+    const int32_t *row = nullptr;
+    long long gain = 0;
+    int lo = 1, hi = 0, nch = 0, j0 = 0;     // written chunk range, chunks, column map
+    // record entry for block q: the largest reverse value right of the block's
+    // smallest column (0, minus infinity biased, below the written range)
+    __device__ __forceinline__ int entry(int q) const {
+        if (!row) return 0;
+        const int jr = j0 - max(0, q * CH - 31);          // as a reversed column
+        const int c = max(0, min(nch - 1, (jr - 1) / CH));
+        if (hi < lo || c < lo) return 0;
+        return row[min(c, hi)];
+    }
+};
 
 __device__ __forceinline__ LabGuide lab_guide(const LabProblem &pr, const LabParams &P, int band, int R)
 {
-    LabGuide g{nullptr, 0};
+    LabGuide g;
     if (!(P.prune && pr.target > 0 && pr.gin) || band >= pr.nbands) return g;
     const long long T = min((long long)pr.n, (long long)(band + 1) * R);
     if ((long long)pr.gin_i0 - T < 0) return g;
@@ -102,15 +115,20 @@ __device__ __forceinline__ LabGuide lab_guide(const LabProblem &pr, const LabPar
     const long long r = (long long)pr.gin_i0 - (k + 1) * (long long)pr.gin_step;
     g.row = pr.gin + (size_t)k * (size_t)(pr.gin_nch + 2);
     g.gain = (long long)P.max_sub * (r - (long long)band * R) + P.slack - BIAS;
+    g.nch = pr.gin_nch;
+    g.j0 = pr.gin_j0;
+    g.lo = g.row[pr.gin_nch];
+    g.hi = g.row[pr.gin_nch + 1];
     return g;
 }
 
 // What a path can still gain, up to the sink, after a frontier node of block q
 // of `band` (every cell the block or a later block of the band computes): the
 // smaller of max_sub per remaining diagonal step less the unavoidable gap
-// columns, and the reverse-record bound.  Non-increasing in q.
+// columns, and the reverse-record bound (entry = g.entry(q), loaded ahead).
+// Non-increasing in q.
 __device__ __forceinline__ long long lab_gain(const LabProblem &pr, const LabParams &P, const LabGuide &g,
-                                              int band, int q, int R)
+                                              int band, int q, int R, int entry)
 {
     const long long dr_hi = (long long)pr.n - (long long)band * R, dr_lo = max(0LL, dr_hi - R);
     const long long jlo = max(0, q * CH - CH), jhi = min(pr.m, q * CH + CH);
@@ -119,12 +137,7 @@ __device__ __forceinline__ long long lab_gain(const LabProblem &pr, const LabPar
     if (dr_lo > dc_hi) gapmin = dr_lo - dc_hi;
     if (dc_lo > dr_hi) gapmin = dc_lo - dr_hi;
     long long gain = (long long)P.max_sub * min(dr_hi, dc_hi) - (long long)P.ge * gapmin;
-    if (g.row) {
-        // smallest column of the block's cells, as a reversed column
-        const int jr = pr.gin_j0 - max(0, q * CH - 31);
-        const int c = max(0, min(pr.gin_nch - 1, (jr - 1) / CH));
-        gain = min(gain, g.gain + rec_at(g.row, pr.gin_nch, c));
-    }
+    if (g.row) gain = min(gain, g.gain + entry);
     return gain;
 }
 
@@ -249,7 +262,7 @@ __global__ void __launch_bounds__(128) lab_kernel(const LabParams P)
         int L = q_lo;
         if (dyn) {
             const long long bh = band == 0 ? BIAS : max(0, BIAS - border_cost(band * R, src_f, go, ge));
-            if (bh + lab_gain(pr, P, gd, band, 0, R) < target) L = max(L, pfirst);
+            if (bh + lab_gain(pr, P, gd, band, 0, R, gd.entry(0)) < target) L = max(L, pfirst);
         }
         if (L > q_hi) {
             // nothing of this band can reach the target
@@ -314,6 +327,9 @@ __global__ void __launch_bounds__(128) lab_kernel(const LabParams P)
         int last_useful = -1;
         for (int q = L; q <= q_hi + 1 && !aborted; ++q) {
             const int buf = q & 1;
+            // record entries for this block and for the chunk flushed at its end,
+            // loaded first so that their latency overlaps the block's work
+            const int e_own = gd.entry(q), e_nx = gd_next.entry(q - 1);
             const bool has_next = q + 1 <= q_hi;
             int nst = 0;
             int4 nv = make_int4(0, 0, LAB_INIT, LAB_INIT);
@@ -335,7 +351,7 @@ __global__ void __launch_bounds__(128) lab_kernel(const LabParams P)
                 mx = max(mx, max(Hlast, updiag));
                 if (q <= q_hi) mx = max(mx, s_in[buf][lane].x);
                 mx = __reduce_max_sync(FULL, mx);
-                skip = (long long)mx + lab_gain(pr, P, gd, band, q, R) < target;
+                skip = (long long)mx + lab_gain(pr, P, gd, band, q, R, e_own) < target;
             }
             ++tiles;
             if (skip) {
@@ -447,7 +463,7 @@ __global__ void __launch_bounds__(128) lab_kernel(const LabParams P)
                 bool useful = true;
                 if (dyn && has_next_band) {
                     hmax = __reduce_max_sync(FULL, hmax);
-                    useful = (long long)hmax + lab_gain(pr, P, gd_next, band + 1, c, R) >= target;
+                    useful = (long long)hmax + lab_gain(pr, P, gd_next, band + 1, c, R, e_nx) >= target;
                 }
                 __syncwarp();
                 if (lane == 0) {
