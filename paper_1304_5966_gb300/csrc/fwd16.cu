@@ -106,6 +106,13 @@ __device__ __forceinline__ GinRow gin_for_band(const FwdProblem &pr, const FwdPa
     return g;
 }
 
+// row of the record this band writes (null: none)
+__device__ __forceinline__ int32_t *rec_row(const FwdProblem &pr, int band)
+{
+    if (!pr.gout || (band + 1) % pr.gstride != 0) return nullptr;
+    return pr.gout + (size_t)((band + 1) / pr.gstride - 1) * (size_t)(pr.gnch + 2);
+}
+
 template <int RPT, bool REL, bool ANCH>
 __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
 {
@@ -113,15 +120,18 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
     __shared__ uint32_t s_out_all[4][2 * CH];   // bottom row, packed int16 (H | F << 16)
     // Grouped launch (anchored): a CTA takes four consecutive tickets, and a band
     // whose successor runs in the same CTA hands its bottom row over through a
-    // ring of GK chunks in shared memory instead of the boundary row in HBM.
-    // The anchored pass follows a narrow band around the path, where the bands
-    // form a chain and the hand-over latency is the pass's time.
+    // ring of GK chunks in shared memory instead of the boundary row in HBM and
+    // its flags.  The anchored pass follows a narrow band around the path, where
+    // the bands form a chain and hand-over latency is part of the pass's time;
+    // the full-width local pass runs faster with its producers decoupled.
     constexpr bool GROUP = ANCH;
     constexpr int GW = 4, GK = 8;
     __shared__ int2 s_ring[GROUP ? GW : 1][GROUP ? GK : 1][CH];   // absolute {H, F}
     __shared__ int s_tag[GROUP ? GW : 1][GROUP ? GK : 1];         // 2 * chunk + useful
     __shared__ int s_need[GW], s_spx[GW], s_spy[GW];              // reader's next chunk; span
     __shared__ int s_base, s_err;
+    __shared__ int s_grun[4];                                     // record row's running maximum
+    __shared__ int32_t *s_grow[4];                                // record row of the warp's band
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     int4 (*s_in)[CH] = s_in_all[wid];
@@ -358,9 +368,11 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
         int published = 0;
         unsigned tiles = 0, pruned = 0;
         // row record of this band's bottom row (running maximum over chunks)
-        int32_t *grow = (pr.gout && (band + 1) % pr.gstride == 0)
-                            ? pr.gout + (size_t)((band + 1) / pr.gstride - 1) * (size_t)(pr.gnch + 2) : nullptr;
-        int grun = INT_MIN;
+        // (its row pointer and running maximum live in shared memory rather than
+        // in registers across the step loop, whose register budget they would
+        // otherwise take)
+        if (lane == 0) { s_grun[wid] = INT_MIN; s_grow[wid] = rec_row(pr, band); }
+        __syncwarp();
         // Anchored with the forward record: any path through a cell of this band
         // that reaches the start crosses a recorded forward row r at or above the
         // band (or starts below it), so what it gains beyond the band's frontier
@@ -377,6 +389,7 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
 
         bool first_pub = false;
         int last_useful = -1, last_flushed = -1, ring_first = 0;
+        int best_seen = 0;
         for (int q = L; q < nblk && !aborted; ++q) {
             const int buf = q % 3;
             // loads whose results are needed only later in the block, issued first
@@ -386,6 +399,10 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
             const int pm_own = gin_own.at(pr.gin_j0 - max(1, q * CH - 62));
             const int pm_nx = gin_nx.at(pr.gin_j0 - max(1, (q - 2) * CH - 62));
             const int stop_seen = (anch && stop && lane == 0) ? ld_volatile(stop) : INT_MAX;
+            // local mode prunes against the running best read one block earlier
+            // (the best only grows, so an older value prunes less, never wrongly)
+            const int best_used = best_seen;
+            if (!anch && lane == 0) best_seen = ld_volatile(pr.best);
             const bool has_next = (q + 1) < nch;
             int nst = 0;
             int2 nv = make_int2(DEAD_H, DEAD_F);
@@ -461,10 +478,7 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
             bool skip = false;
             if (P.prune) {
                 int pthr = target;
-                if (!anch) {
-                    if (lane == 0) pthr = ld_volatile(pr.best);
-                    pthr = __shfl_sync(FULL, pthr, 0);
-                }
+                if (!anch) pthr = __shfl_sync(FULL, best_used, 0);
                 uint32_t mx2 = Hlast;
 #pragma unroll
                 for (int k = 0; k < RPT; ++k) mx2 = REL ? vmax16(mx2, Hl[k]) : __vimax_s16x2_relu(mx2, Hl[k]);
@@ -678,11 +692,8 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                     rec = oh;
                 }
                 int cmax = 0;
+                int32_t *const grow = s_grow[wid];
                 if (grow || dyn) cmax = __reduce_max_sync(FULL, rec);
-                if (grow) {
-                    grun = max(grun, cmax);
-                    if (lane == 0) grow[c] = grun;
-                }
                 // can a value of this chunk still reach the target from the next band?
                 bool useful = true;
                 if (dyn && band + 1 < pr.nbands) {
@@ -711,7 +722,7 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                         if (!__shfl_sync(FULL, ok, 0)) { aborted = true; break; }
                         s_ring[GROUP ? wid : 0][GROUP ? c % GK : 0][lane] = outv;
                         __syncwarp();
-                        if (lane == 0) {
+                        if (lane == 0 && band != P.fault_band) {
                             __threadfence_block();
                             ((volatile int *)s_tag[GROUP ? wid : 0])[GROUP ? c % GK : 0] = 2 * c + (useful ? 1 : 0);
                             if (dyn && useful && !first_pub) vspx[wid] = c;
@@ -724,8 +735,15 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                         if (dyn && useful && !first_pub) st_release(&pr.span[band].x, c);
                     }
                 }
+                // the record entry goes out after the release, which then does not
+                // wait for it
+                if (grow && lane == 0) {
+                    const int g = max(s_grun[wid], cmax);
+                    s_grun[wid] = g;
+                    grow[c] = g;
+                }
                 if (useful) { first_pub = true; last_useful = c; }
-                last_flushed = c;
+                if (ANCH) last_flushed = c;
             }
             if (!anch) {
                 const int wb = __reduce_max_sync(FULL, max(best_lo, best_hi));
@@ -757,7 +775,11 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                 st_release(&pr.span[band].y, last_useful);
             }
         }
-        if (grow && lane == 0) { grow[nch] = L; grow[nch + 1] = last_flushed; }
+        if (lane == 0) {
+            int32_t *const grow = s_grow[wid];
+            // a local band flushes every chunk; an anchored one may stop early
+            if (grow) { grow[nch] = L; grow[nch + 1] = ANCH ? last_flushed : nch - 1; }
+        }
         // band result over the 64 virtual lanes (low halves hold the smaller rows)
         int vs = best_lo, vr = rb_lo + (bk_lo < RPT ? bk_lo : 0) + 1, vc = bc_lo + 1, ok = best_lo > binit;
         {
