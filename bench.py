@@ -48,21 +48,26 @@ def _args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-extras", action="store_true", help="skip the batch / plain comparisons")
-    p.add_argument("--workload", default="pair_5m", choices=["pair_5m", "score_500k", "score_2m"],
-                   help="score_500k / score_2m: forward pass alone on a 500 kbp pair / a 2 Mbp x 1 Mbp "
-                        "homologous pair (profiling cases)")
+    p.add_argument("--workload", default="pair_5m", choices=["pair_5m", "score_500k", "score_2m", "score_5m_1m"],
+                   help="score_500k / score_2m / score_5m_1m: forward pass alone on a 500 kbp pair, a 2 Mbp x "
+                        "1 Mbp homologous pair, or the first 5,000,000 x 1,000,000 of the bench pair (the bench's "
+                        "band height) -- profiling cases")
     p.add_argument("--workspace-gb", type=int, default=0, help="device workspace (default by workload)")
     return p.parse_args()
 
 
 def run_profile_case(args):
-    """Cases for ncu: sw_score on a 500,000 x ~500,000 homologous pair (score_500k)
-    or on the first 2,000,000 x 1,000,000 of a homologous pair (score_2m, enough
-    bands and columns to fill the band pipeline)."""
+    """Cases for ncu: sw_score on a 500,000 x ~500,000 homologous pair (score_500k),
+    on the first 2,000,000 x 1,000,000 of a homologous pair (score_2m, enough
+    bands and columns to fill the band pipeline) or on the first 5,000,000 x
+    1,000,000 of the bench pair (score_5m_1m: the bench's 1,024-row bands)."""
     import torch
     import paper_1304_5966_gb300 as sw
     from gen import synth
-    if args.workload == "score_2m":
+    if args.workload == "score_5m_1m":
+        a, b = synth.pair_5m()
+        b = b[:1_000_000].copy()
+    elif args.workload == "score_2m":
         a, b = synth.pair_homologous(2_000_000, seed=13, gc_permille=410)
         b = b[:1_000_000].copy()
     else:
@@ -259,7 +264,7 @@ def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload in ("score_500k", "score_2m"):
+    if args.workload in ("score_500k", "score_2m", "score_5m_1m"):
         return run_profile_case(args)
     ws, rank, local = _dist()
     import numpy as np
@@ -371,11 +376,13 @@ def main():
     line = {
         "metric": "GCUPS", "value": round(value, 2), "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 1), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "int16", "data": "synthetic",
         "config": {"workload": f"pair_5m: {n} x {m} DNA pair (GC 41%, tandem repeats, 10% subst, 1% ins, "
                                f"1% del, 20 kbp inversion, 50 kbp deletion); sw_align = score + end, "
                                f"start, CIGAR; match +1, mismatch -3, gap 5 + 2(k-1)",
                    "l2": "flushed before every step (256 MiB write); step working set < L2",
+                   "arithmetic": "exact integer scores: forward and start passes on int16x2 DPX lanes with "
+                                 "per-warp offsets, int32 boundary rows and reconstruction",
                    "score": r.score, "a": [r.a_begin, r.a_end], "b": [r.b_begin, r.b_end],
                    "cigar_len": len(r.cigar or ""), "parallelism": f"replicas x{ws}"},
         "phases_ms": {"forward": round(r.stats["ms_forward"], 1), "start": round(r.stats["ms_start"], 1),
