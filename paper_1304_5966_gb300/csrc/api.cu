@@ -211,7 +211,7 @@ static int run_forward_impl(sw_ctx *ctx, const SchemeDev &sc, const std::vector<
         return set_cuda_error(ctx, e, "forward setup");
     // local: bus row 0 = {0, -go}; anchored: -inf everywhere (biased 0)
     const bool anch = jobs[0].mode == FWD_ANCHORED;
-    if ((e = fwd_init_launch(dprobs, np, hp.data(), 0, anch ? 0 : -sc.go, s)))
+    if ((e = fwd_init_launch(dprobs, np, hp.data(), 0, anch ? 0 : -sc.go, lane16, s)))
         return set_cuda_error(ctx, e, "forward init");
     FwdParams P;
     std::memset(&P, 0, sizeof P);

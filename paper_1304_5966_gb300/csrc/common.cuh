@@ -82,6 +82,31 @@ __device__ __forceinline__ int wait_flag(const int *flag, int need, int *err,
     }
 }
 
+// Self-validating boundary-row entry (int16x2 kernel): H as int32, how far F
+// lies below H (clamped at 0xffff: farther below, F - ge stays under H - go for
+// any gap open up to 0xffff, so F no longer matters), and the tag of the band
+// that wrote it, ((band & 0x7fff) << 1) | useful.  One 64-bit word, read and
+// written whole, so a reader that finds its predecessor's tag has its data.
+__host__ __device__ __forceinline__ unsigned bus_tag(int band, bool useful) {
+    return ((unsigned)band & 0x7fffu) << 1 | (useful ? 1u : 0u);
+}
+__host__ __device__ __forceinline__ unsigned long long busw_pack(int h, int f, unsigned tag) {
+    const long long d = (long long)h - f;
+    const unsigned dd = d > 0xffff ? 0xffffu : (unsigned)d;
+    return (unsigned long long)(unsigned)h | ((unsigned long long)dd << 32) | ((unsigned long long)(tag & 0xffffu) << 48);
+}
+__device__ __forceinline__ int busw_h(unsigned long long w) { return (int)(unsigned)(w & 0xffffffffull); }
+__device__ __forceinline__ int busw_f(unsigned long long w) { return busw_h(w) - (int)((w >> 32) & 0xffffu); }
+__device__ __forceinline__ unsigned busw_tag(unsigned long long w) { return (unsigned)(w >> 48); }
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+
 // Published-range words (the first and last useful chunk of a band, see the
 // label and anchored passes): not yet written, and "no useful chunk".
 constexpr int SPAN_UNPUB = INT_MIN;

@@ -277,12 +277,19 @@ __global__ void __launch_bounds__(128) fwd_kernel(const FwdParams P)
 }
 
 // ---------------------------------------------------------------------------
-__global__ void fwd_init_kernel(FwdProblem *probs, int nprobs, int h0, int f0)
+__global__ void fwd_init_kernel(FwdProblem *probs, int nprobs, int h0, int f0, int packed)
 {
     const int p = blockIdx.x;
     if (p >= nprobs) return;
     FwdProblem pr = probs[p];
-    for (int j = threadIdx.x; j < pr.m; j += blockDim.x) pr.bus[j] = make_int2(h0, f0);
+    // row 0: {H, F} pairs (int32 lanes) or self-validating words tagged as
+    // written by band -1 (int16x2 lanes)
+    if (packed) {
+        const unsigned long long w = busw_pack(h0, f0, bus_tag(-1, true));
+        for (int j = threadIdx.x; j < pr.m; j += blockDim.x) ((unsigned long long *)pr.bus)[j] = w;
+    } else {
+        for (int j = threadIdx.x; j < pr.m; j += blockDim.x) pr.bus[j] = make_int2(h0, f0);
+    }
     const int nch = (pr.m + CH - 1) / CH;
     for (int c = threadIdx.x; c < nch; c += blockDim.x) pr.flags[c] = -1;
     for (int b = threadIdx.x; b < pr.nbands; b += blockDim.x) {
@@ -369,11 +376,11 @@ cudaError_t fwd_occupancy(int rpt, bool p2, int threads, int *n)
     }
 }
 
-cudaError_t fwd_init_launch(FwdProblem *probs_dev, int nprobs, const FwdProblem *, int h0, int f0,
+cudaError_t fwd_init_launch(FwdProblem *probs_dev, int nprobs, const FwdProblem *, int h0, int f0, bool packed,
                             cudaStream_t s)
 {
     if (nprobs <= 0) return cudaSuccess;
-    fwd_init_kernel<<<nprobs, 256, 0, s>>>(probs_dev, nprobs, h0, f0);
+    fwd_init_kernel<<<nprobs, 256, 0, s>>>(probs_dev, nprobs, h0, f0, packed ? 1 : 0);
     return cudaGetLastError();
 }
 

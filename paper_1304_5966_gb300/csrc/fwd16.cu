@@ -171,10 +171,9 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
         const bool transposed = pr.transposed != 0;
         constexpr bool anch = REL && ANCH;    // every problem of an anchored launch is anchored
         const uint8_t *__restrict__ bseq = pr.b;
-        int2 *__restrict__ bus = pr.bus;
-        int *__restrict__ flags = pr.flags;
+        unsigned long long *__restrict__ busw = (unsigned long long *)pr.bus;
         int *stop = anch ? pr.stop_band : nullptr;
-        const int need = band - 1;
+        const unsigned want_tag = (unsigned)(band - 1) & 0x7fffu;   // tag of the row above
         const int guard = 32767 - P.max_sub;
         const int target = pr.target;
         // dead values of skipped cells, absolute (what the boundary row carries)
@@ -249,29 +248,48 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
             release_reader();
             continue;
         }
-        // input chunk c: 1 useful (read it), 0 dead, 2 not released yet
-        auto in_status = [&](int c) -> int {
+        // Input chunk c, called by the whole warp: returns 1 (useful; v holds the
+        // lane's column), 0 (dead: minus infinity, no data needed) or 2 (not yet
+        // written).  From the ring: the producer's tag for the chunk.  From the
+        // boundary row: every word carries its writer's band, so the data load is
+        // also the readiness test (no flag, no fence).
+        auto in_status = [&](int c, int2 &v) -> int {
             if (c < pfirst) return 0;
             if (pred_in) {
-                const int t = vtag[c % GK];
-                if ((t >> 1) == c) { __threadfence_block(); return t & 1; }
-                const int y = vspy[wid - 1];
-                if (y != SPAN_UNPUB && c > y) return 0;
-                return 2;
+                int st = 2;
+                if (lane == 0) {
+                    const int t = vtag[c % GK];
+                    if ((t >> 1) == c) { __threadfence_block(); st = t & 1; }
+                    else {
+                        const int y = vspy[wid - 1];
+                        if (y != SPAN_UNPUB && c > y) st = 0;
+                    }
+                }
+                st = __shfl_sync(FULL, st, 0);
+                if (st == 1) {
+                    __syncwarp();      // orders the ring reads after lane 0's view of the tag
+                    v = s_ring[GROUP ? wid - 1 : 0][GROUP ? c % GK : 0][lane];
+                }
+                return st;
             }
-            const int v = ld_acquire(&flags[c]);
-            if (v >= 2 * need) return v & 1;
+            const int col = c * CH + lane;
+            unsigned long long w = 0;
+            bool ok = true;
+            if (col < m) {
+                w = ld_relaxed_u64(&busw[col]);
+                ok = (busw_tag(w) >> 1) == want_tag;
+            }
+            if (__all_sync(FULL, ok)) {
+                v = make_int2(busw_h(w), busw_f(w));
+                return __shfl_sync(FULL, (int)(busw_tag(w) & 1u), 0);   // column c * CH < m
+            }
             if (pred_last) {
-                const int y = ld_acquire(pred_last);
+                int y = 0;
+                if (lane == 0) y = ld_acquire(pred_last);
+                y = __shfl_sync(FULL, y, 0);
                 if (y != SPAN_UNPUB && c > y) return 0;
             }
             return 2;
-        };
-        // one column of input chunk c (st = 1: released and useful); ring reads
-        // follow a __syncwarp after the status broadcast, which orders them
-        // after lane 0's view of the tag
-        auto in_load = [&](int c, int col) -> int2 {
-            return pred_in ? s_ring[GROUP ? wid - 1 : 0][GROUP ? c % GK : 0][lane] : bus[col];
         };
         // tell the predecessor that chunks before `next` have been read
         auto mark_read = [&](int next) {
@@ -280,9 +298,9 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                 if (lane == 0) { __threadfence_block(); vneed[wid] = next; }
             }
         };
-        // the same, waiting (bounded) for the release; -1 when the band must stop
-        auto wait_status = [&](int c) -> int {
-            int st = in_status(c);
+        // the same, waiting (bounded) for the chunk; -1 when the band must stop
+        auto wait_status = [&](int c, int2 &v) -> int {
+            int st = in_status(c, v);
             if (st != 2) return st;
             const unsigned long long t0 = globaltimer();
             unsigned ns = 64;
@@ -293,27 +311,25 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                 } else {
                     __nanosleep(20);
                 }
-                st = in_status(c);
+                st = in_status(c, v);
                 if (st != 2) return st;
-                if (ld_volatile(P.err)) return -1;
-                if (stop && ld_volatile(stop) < band) return -1;
-                if (globaltimer() - t0 > P.timeout_ns) { atomicCAS(P.err, 0, DEV_ETIMEOUT); return -1; }
+                int quit = 0;
+                if (lane == 0) {
+                    if (ld_volatile(P.err) || (stop && ld_volatile(stop) < band)) quit = 1;
+                    else if (globaltimer() - t0 > P.timeout_ns) { atomicCAS(P.err, 0, DEV_ETIMEOUT); quit = 1; }
+                }
+                if (__shfl_sync(FULL, quit, 0)) return -1;
             }
         };
         {
-            int st = 0;
-            if (lane == 0) st = wait_status(L);
-            st = __shfl_sync(FULL, st, 0);
+            int2 v = make_int2(DEAD_H, DEAD_F);
+            const int st = wait_status(L, v);
             if (st < 0) aborted = true;
             else {
-                int2 v = make_int2(DEAD_H, DEAD_F);
+                if (st != 1 || L * CH + lane >= m) v = make_int2(DEAD_H, DEAD_F);
                 uint32_t sel = 0;
                 const int col = L * CH + lane;
-                if (pred_in) __syncwarp();
-                if (col < m) {
-                    if (st == 1) v = in_load(L, col);
-                    sel = sel_lo8(bseq[col]);
-                }
+                if (col < m) sel = sel_lo8(bseq[col]);
                 s_in[L % 3][lane] = make_int4(v.x, v.y, (int)sel, 0);
             }
             mark_read(L + 1);
@@ -408,15 +424,22 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
             int2 nv = make_int2(DEAD_H, DEAD_F);
             uint32_t nsel = 0;
             const int ncol = (q + 1) * CH + lane;
-            if (has_next) {
-                if (lane == 0) nst = in_status(q + 1);
-                nst = __shfl_sync(FULL, nst, 0);
+            // Chunk q + 1: from the ring, test now; from the boundary row, issue the
+            // word loads now and test their tags after the block's steps, so the
+            // load latency overlaps the steps.
+            unsigned long long wnext = 0;
+            int cnext = 0;
+            const bool from_bus = has_next && !pred_in && q + 1 >= pfirst;
+            if (has_next && ncol < m) {
+                cnext = bseq[ncol];
+                if (from_bus) wnext = ld_relaxed_u64(&busw[ncol]);
+            }
+            nst = 2;
+            if (has_next && !from_bus) {
+                int2 v;
+                nst = in_status(q + 1, v);
                 if (nst != 2) {
-                    if (pred_in) __syncwarp();
-                    if (ncol < m) {
-                        if (nst == 1) nv = in_load(q + 1, ncol);
-                        nsel = sel_lo8(bseq[ncol]);
-                    }
+                    if (ncol < m && nst == 1) nv = v;
                     mark_read(q + 2);
                 }
             }
@@ -658,18 +681,21 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                 }
             }
             if (has_next) {
-                if (nst == 2) {
-                    int st = 0;
-                    if (lane == 0) st = wait_status(q + 1);
-                    st = __shfl_sync(FULL, st, 0);
-                    if (st < 0) { aborted = true; break; }
-                    if (pred_in) __syncwarp();
-                    if (ncol < m) {
-                        if (st == 1) nv = in_load(q + 1, ncol);
-                        nsel = sel_lo8(bseq[ncol]);
+                if (from_bus) {
+                    const bool ok = ncol >= m || (busw_tag(wnext) >> 1) == want_tag;
+                    if (__all_sync(FULL, ok)) {
+                        nst = __shfl_sync(FULL, (int)(busw_tag(wnext) & 1u), 0);
+                        if (nst == 1 && ncol < m) nv = make_int2(busw_h(wnext), busw_f(wnext));
                     }
+                }
+                if (nst == 2) {
+                    int2 v;
+                    const int st = wait_status(q + 1, v);
+                    if (st < 0) { aborted = true; break; }
+                    if (ncol < m && st == 1) nv = v;
                     mark_read(q + 2);
                 }
+                if (ncol < m) nsel = sel_lo8((uint32_t)cnext);
                 s_in[(q + 1) % 3][lane] = make_int4(nv.x, nv.y, (int)nsel, 0);
             }
             __syncwarp();
@@ -688,7 +714,6 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                         of = (of <= REL_FLOOR) ? DEAD_F : of + Ou;
                     }
                     outv = make_int2(oh, of);
-                    if (!succ_in) bus[col] = outv;
                     rec = oh;
                 }
                 int cmax = 0;
@@ -729,11 +754,13 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                         }
                     }
                 } else {
+                    // one self-validating word per column (a band that never
+                    // publishes, for testing, writes nothing)
+                    if (col < m && band != P.fault_band)
+                        st_relaxed_u64(&busw[col], busw_pack(outv.x, outv.y, bus_tag(band, useful)));
                     __syncwarp();
-                    if (lane == 0 && band != P.fault_band) {
-                        st_release(&flags[c], 2 * band + (useful ? 1 : 0));
-                        if (dyn && useful && !first_pub) st_release(&pr.span[band].x, c);
-                    }
+                    if (lane == 0 && band != P.fault_band && dyn && useful && !first_pub)
+                        st_release(&pr.span[band].x, c);
                 }
                 // the record entry goes out after the release, which then does not
                 // wait for it

@@ -18,7 +18,8 @@ struct FwdProblem {          // one alignment problem, device resident
     int32_t mode;            // FwdMode
     int32_t target;          // FWD_ANCHORED: biased value sought (BIAS + S)
     int32_t transposed;      // 1: rows are the user's B (tie rule column-first)
-    int2 *bus;               // m entries {H, F} of the row above the current band
+    int2 *bus;               // m entries: {H, F} of the row above the current band (int32 lanes),
+                             // one self-validating 64-bit word each (int16x2 lanes)
     int32_t *flags;          // ceil(m/32): 2 * (last band that released chunk c) + useful bit
     int2 *span;              // nbands: {first, last} useful chunk of each band's bottom row
     int32_t *best;           // running best for pruning (FWD_LOCAL)
@@ -72,8 +73,9 @@ cudaError_t fwd_launch(const FwdParams &p, int rpt, bool two_word_profile, int c
                        int threads, cudaStream_t s);
 cudaError_t fwd_occupancy(int rpt, bool two_word_profile, int threads, int *ctas_per_sm);
 // fills bus with {h0, f0} and flags with -1 etc. for a set of problems
+// packed: the boundary row holds the int16x2 kernel's self-validating words
 cudaError_t fwd_init_launch(FwdProblem *probs_dev, int nprobs, const FwdProblem *probs_host,
-                            int h0, int f0, cudaStream_t s);
+                            int h0, int f0, bool packed, cudaStream_t s);
 // per-problem reduction of band results -> out[p] = {score, row, col, found}
 cudaError_t fwd_reduce_launch(const FwdProblem *probs_dev, int nprobs, int4 *out,
                               cudaStream_t s);
