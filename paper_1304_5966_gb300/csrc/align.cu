@@ -50,7 +50,11 @@ static int run_label_level(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, 
     cross.assign(np, {});
     sinkv.assign(np, 0);
     if (np == 0) return SW_OK;
-    const int R = 32 * LAB_RPT;
+    // a level bounded by the reverse record runs on thin lanes
+    bool guided_level = false;
+    for (auto *g : guides) guided_level |= g != nullptr;
+    const int rpt = guided_level ? LAB_RPT_GUIDED : LAB_RPT;
+    const int R = 32 * rpt;
     Scope s(ctx->arena);
     std::vector<LabProblem> hp(np);
     int64_t ntk = 0;
@@ -154,11 +158,11 @@ static int run_label_level(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, 
     int per_sm = 1;
     cudaEvent_t t0 = ctx->ev[8], t1 = ctx->ev[9];
     if (ctx->opt.trace) cudaEventRecord(t0, st);
-    lab_occupancy(!any_t, p2, &per_sm);
+    lab_occupancy(rpt, !any_t, p2, &per_sm);
     int ctas = std::max(1, per_sm) * ctx->sms;
     ctas = (int)std::min<int64_t>(ctas, (ntk + 3) / 4);
-    if ((e = lab_launch(P, !any_t, p2, ctas, st))) return set_cuda_error(ctx, e, "label launch");
-    if ((e = lab_walk_launch(dprobs, np, sc.go, sc.ge, dcross, maxnck, dres, st)))
+    if ((e = lab_launch(P, rpt, !any_t, p2, ctas, st))) return set_cuda_error(ctx, e, "label launch");
+    if ((e = lab_walk_launch(dprobs, np, R, sc.go, sc.ge, dcross, maxnck, dres, st)))
         return set_cuda_error(ctx, e, "label walk");
     ctx->launches += 3;
     std::vector<int4> hc((size_t)np * maxnck), hr(np);

@@ -564,19 +564,35 @@ static cudaError_t lab_one(const LabParams &p, int ctas, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t lab_launch(const LabParams &p, bool pref_vert, bool p2, int ctas, cudaStream_t s)
+template <int RPT>
+static cudaError_t lab_launch_rpt(const LabParams &p, bool pref_vert, bool p2, int ctas, cudaStream_t s)
 {
-    if (pref_vert) return p2 ? lab_one<LAB_RPT, true, true>(p, ctas, s) : lab_one<LAB_RPT, true, false>(p, ctas, s);
-    return p2 ? lab_one<LAB_RPT, false, true>(p, ctas, s) : lab_one<LAB_RPT, false, false>(p, ctas, s);
+    if (pref_vert) return p2 ? lab_one<RPT, true, true>(p, ctas, s) : lab_one<RPT, true, false>(p, ctas, s);
+    return p2 ? lab_one<RPT, false, true>(p, ctas, s) : lab_one<RPT, false, false>(p, ctas, s);
 }
 
-cudaError_t lab_occupancy(bool pref_vert, bool p2, int *n)
+cudaError_t lab_launch(const LabParams &p, int rpt, bool pref_vert, bool p2, int ctas, cudaStream_t s)
+{
+    if (rpt == LAB_RPT) return lab_launch_rpt<LAB_RPT>(p, pref_vert, p2, ctas, s);
+    if (LAB_RPT_GUIDED != LAB_RPT && rpt == LAB_RPT_GUIDED) return lab_launch_rpt<LAB_RPT_GUIDED>(p, pref_vert, p2, ctas, s);
+    return cudaErrorInvalidValue;
+}
+
+template <int RPT>
+static cudaError_t lab_occupancy_rpt(bool pref_vert, bool p2, int *n)
 {
     if (pref_vert)
-        return p2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lab_kernel<LAB_RPT, true, true>, 128, 0)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lab_kernel<LAB_RPT, true, false>, 128, 0);
-    return p2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lab_kernel<LAB_RPT, false, true>, 128, 0)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lab_kernel<LAB_RPT, false, false>, 128, 0);
+        return p2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lab_kernel<RPT, true, true>, 128, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lab_kernel<RPT, true, false>, 128, 0);
+    return p2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lab_kernel<RPT, false, true>, 128, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lab_kernel<RPT, false, false>, 128, 0);
+}
+
+cudaError_t lab_occupancy(int rpt, bool pref_vert, bool p2, int *n)
+{
+    if (rpt == LAB_RPT) return lab_occupancy_rpt<LAB_RPT>(pref_vert, p2, n);
+    if (LAB_RPT_GUIDED != LAB_RPT && rpt == LAB_RPT_GUIDED) return lab_occupancy_rpt<LAB_RPT_GUIDED>(pref_vert, p2, n);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t lab_init_launch(LabProblem *probs, int nprobs, int go, int ge, cudaStream_t s)
@@ -586,11 +602,11 @@ cudaError_t lab_init_launch(LabProblem *probs, int nprobs, int go, int ge, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t lab_walk_launch(const LabProblem *probs, int nprobs, int go, int ge, int4 *out, int stride,
+cudaError_t lab_walk_launch(const LabProblem *probs, int nprobs, int R, int go, int ge, int4 *out, int stride,
                             int4 *res, cudaStream_t s)
 {
     if (nprobs <= 0) return cudaSuccess;
-    lab_walk_kernel<<<(nprobs + 127) / 128, 128, 0, s>>>(probs, nprobs, 32 * LAB_RPT, go, ge, out, stride, res);
+    lab_walk_kernel<<<(nprobs + 127) / 128, 128, 0, s>>>(probs, nprobs, R, go, ge, out, stride, res);
     return cudaGetLastError();
 }
 

@@ -11,6 +11,11 @@ constexpr int ST_H = 0, ST_E = 1, ST_F = 2;
 // crossing-edge label = (source column << 2) | type
 constexpr int LAB_DIAG = 0, LAB_OPEN = 1, LAB_EXT = 2, LAB_INIT = 3;
 constexpr int LAB_RPT = 8;            // rows per thread of the label pass
+// Rows per thread of a label pass bounded by the reverse record.  Its bands
+// form a chain along a narrow band around the path; measured on the 5 Mbp
+// pair, each chunk of that chain is dominated by the hand-over between bands
+// rather than by the rows, so thinner lanes (2 or 4 rows) only add bands.
+constexpr int LAB_RPT_GUIDED = LAB_RPT;
 
 struct LabProblem {
     const uint8_t *a;      // kernel rows, n codes
@@ -48,10 +53,11 @@ struct LabParams {
     unsigned long long timeout_ns;
 };
 
-cudaError_t lab_launch(const LabParams &p, bool pref_vert, bool p2, int ctas, cudaStream_t s);
-cudaError_t lab_occupancy(bool pref_vert, bool p2, int *n);
+// rpt: LAB_RPT or LAB_RPT_GUIDED
+cudaError_t lab_launch(const LabParams &p, int rpt, bool pref_vert, bool p2, int ctas, cudaStream_t s);
+cudaError_t lab_occupancy(int rpt, bool pref_vert, bool p2, int *n);
 cudaError_t lab_init_launch(LabProblem *probs, int nprobs, int go, int ge, cudaStream_t s);
-cudaError_t lab_walk_launch(const LabProblem *probs, int nprobs, int go, int ge, int4 *out, int stride,
+cudaError_t lab_walk_launch(const LabProblem *probs, int nprobs, int R, int go, int ge, int4 *out, int stride,
                             int4 *res, cudaStream_t s);
 
 // full-matrix leaves: one CTA each, pointers in shared memory, greedy traceback
