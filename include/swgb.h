@@ -93,6 +93,8 @@ typedef struct {
     int64_t kernel_launches;   /* kernels this call launched */
     int64_t start_cells;       /* cells computed by the start-point pass */
     int64_t align_cells;       /* cells computed by the reconstruction label passes */
+    int32_t band_rows;         /* rows per band of the forward pass (int16x2 batch: as tuned) */
+    int32_t tuned;             /* batch: 1 when this call timed the candidate band heights */
 } sw_stats;
 
 typedef struct {
@@ -137,7 +139,13 @@ const char *sw_strerror(int status);
  *   SW_OPT_TRACE            1 = print one line per device pass to stderr (kernel
  *                           time, cells computed, chunks visited and pruned); also
  *                           switched on at context creation by the environment
- *                           variable SWGB_TRACE=1. */
+ *                           variable SWGB_TRACE=1.
+ *   SW_OPT_AUTOTUNE         sw_align_batch: 1 (default) = the first call of a batch
+ *                           shape (pair count, mean and largest length, rounded to
+ *                           powers of two) times each band height of the int16x2
+ *                           forward pass on the whole batch and keeps the fastest
+ *                           for later calls of that shape; 0 = chosen by size.
+ *                           The results are identical either way. */
 enum {
     SW_OPT_ROWS_PER_THREAD = 1,
     SW_OPT_WARPS_PER_SM = 2,
@@ -146,7 +154,8 @@ enum {
     SW_OPT_CKPT_BANDS = 5,
     SW_OPT_LEAF_CELLS = 6,
     SW_OPT_FORWARD_LANES = 7,
-    SW_OPT_TRACE = 8
+    SW_OPT_TRACE = 8,
+    SW_OPT_AUTOTUNE = 9
 };
 int sw_ctx_set_option(sw_ctx *ctx, int option, int64_t value);
 

@@ -31,7 +31,7 @@ SW_FLAG_NO_PRUNE = 0x4
 SW_FLAG_FORCE_INT32 = 0x8
 SW_FLAG_FORCE_INT16 = 0x10
 SW_OPT_ROWS_PER_THREAD, SW_OPT_WARPS_PER_SM, SW_OPT_TIMEOUT_MS, SW_OPT_FAULT_BAND, \
-    SW_OPT_CKPT_BANDS, SW_OPT_LEAF_CELLS, SW_OPT_FORWARD_LANES, SW_OPT_TRACE = range(1, 9)
+    SW_OPT_CKPT_BANDS, SW_OPT_LEAF_CELLS, SW_OPT_FORWARD_LANES, SW_OPT_TRACE, SW_OPT_AUTOTUNE = range(1, 10)
 
 
 class SwError(RuntimeError):
@@ -53,13 +53,23 @@ class _Stats(ctypes.Structure):
                 ("ms_forward", ctypes.c_float), ("ms_start", ctypes.c_float),
                 ("ms_align", ctypes.c_float), ("fwd_cells", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("start_cells", ctypes.c_int64),
-                ("align_cells", ctypes.c_int64)]
+                ("align_cells", ctypes.c_int64), ("band_rows", ctypes.c_int32), ("tuned", ctypes.c_int32)]
 
 
 class _Result(ctypes.Structure):
     _fields_ = [("score", ctypes.c_int64), ("a_begin", ctypes.c_int64), ("a_end", ctypes.c_int64),
                 ("b_begin", ctypes.c_int64), ("b_end", ctypes.c_int64),
                 ("cigar", ctypes.c_void_p), ("cigar_len", ctypes.c_int64), ("stats", _Stats)]
+
+
+# numpy view of a _Result array (same layout): score, coordinates, the CIGAR
+# pointer and the per-pair cell count, read in bulk for large batches
+_RESULT_DTYPE = np.dtype({"names": ["score", "a_begin", "a_end", "b_begin", "b_end", "cigar", "cells"],
+                          "formats": ["<i8"] * 5 + ["<u8", "<i8"],
+                          "offsets": [_Result.score.offset, _Result.a_begin.offset, _Result.a_end.offset,
+                                      _Result.b_begin.offset, _Result.b_end.offset, _Result.cigar.offset,
+                                      _Result.stats.offset + _Stats.cells.offset],
+                          "itemsize": ctypes.sizeof(_Result)})
 
 
 class _Pair(ctypes.Structure):
@@ -241,28 +251,64 @@ def sw_score_plain(ctx: Context, a, b, scheme: Scheme | None = None, flags: int 
     return _pairwise(lib().sw_score_plain, ctx, a, b, scheme, flags)
 
 
+def _host_pairs(pairs):
+    """sw_pair records of host numpy uint8 pairs as one int64 array (the fast
+    path for large batches), or None when any sequence is something else."""
+    u8 = np.dtype(np.uint8)
+    rows = []
+    for a, b in pairs:
+        if (a.__class__ is not np.ndarray or b.__class__ is not np.ndarray or a.dtype != u8 or b.dtype != u8
+                or not a.flags.c_contiguous or not b.flags.c_contiguous):
+            return None
+        rows.append((a.ctypes.data, a.size, b.ctypes.data, b.size))
+    return np.array(rows, dtype=np.int64).reshape(len(rows), 4)
+
+
 def sw_align_batch(ctx: Context, pairs, scheme: Scheme | None = None, flags: int = 0):
     """Many pairs in one persistent launch; returns one Result per pair, in order."""
-    cp = (_Pair * max(1, len(pairs)))()
     keep = []
     dev = None
-    for k, (a, b) in enumerate(pairs):
-        pa, n, da, ka = _seq(a)
-        pb, m, db, kb = _seq(b)
-        if da != db or (dev is not None and dev != da):
-            raise ValueError("all sequences must be host, or all device")
-        dev = da
-        keep += [ka, kb]
-        cp[k] = _Pair(pa, n, pb, m)
+    packed = _host_pairs(pairs) if len(pairs) else None
+    if packed is not None:
+        keep.append(packed)
+        cp = packed.ctypes.data_as(ctypes.POINTER(_Pair))
+    else:
+        cp = (_Pair * max(1, len(pairs)))()
+        for k, (a, b) in enumerate(pairs):
+            pa, n, da, ka = _seq(a)
+            pb, m, db, kb = _seq(b)
+            if da != db or (dev is not None and dev != da):
+                raise ValueError("all sequences must be host, or all device")
+            dev = da
+            keep += [ka, kb]
+            cp[k] = _Pair(pa, n, pb, m)
     if dev:
         flags |= SW_FLAG_DEVICE_INPUT
     sch, kk = (scheme or DNA)._c()
     outs = (_Result * max(1, len(pairs)))()
     st = lib().sw_align_batch(ctx.handle, cp, len(pairs), ctypes.byref(sch), flags, outs)
     _check(ctx, st)
-    res = [_result(outs[k]) for k in range(len(pairs))]
-    for k in range(len(pairs)):
-        lib().sw_result_free(ctypes.byref(outs[k]))
+    return _batch_results(outs, len(pairs))
+
+
+def _batch_results(outs, count: int):
+    """Results of a batch call: the call's statistics are in the first result
+    (every later one carries its cell count only); read through one array view."""
+    if count == 0:
+        return []
+    view = np.frombuffer((ctypes.c_char * (ctypes.sizeof(_Result) * count)).from_buffer(outs),
+                         dtype=_RESULT_DTYPE, count=count)
+    score, a0, a1 = view["score"].tolist(), view["a_begin"].tolist(), view["a_end"].tolist()
+    b0, b1, cells = view["b_begin"].tolist(), view["b_end"].tolist(), view["cells"].tolist()
+    has_cigar = view["cigar"].any()
+    res = []
+    for k in range(count):
+        cig = None
+        if has_cigar and outs[k].cigar:
+            cig = ctypes.string_at(outs[k].cigar, outs[k].cigar_len).decode()
+            lib().sw_result_free(ctypes.byref(outs[k]))
+        st = {f: getattr(outs[0].stats, f) for f, _ in _Stats._fields_} if k == 0 else {"cells": cells[k]}
+        res.append(Result(score[k], a0[k], a1[k], b0[k], b1[k], cig, st))
     return res
 
 

@@ -98,6 +98,7 @@ static bool rel16_fits(const SchemeDev &sc, int rpt)
 {
     if (sc.alphabet > 4) return false;
     if (sc.go + sc.ge - sc.min_sub > 255 || sc.max_sub > 127) return false;
+    if (sc.go - sc.ge > 255) return false;      // the anchored passes' boundary words keep 8 bits of F
     const int64_t spread = (int64_t)(64 * rpt + 96) * (sc.go + sc.max_sub) + 64 * sc.max_sub;
     return spread <= 44000;
 }
@@ -211,7 +212,7 @@ static int run_forward_impl(sw_ctx *ctx, const SchemeDev &sc, const std::vector<
         return set_cuda_error(ctx, e, "forward setup");
     // local: bus row 0 = {0, -go}; anchored: -inf everywhere (biased 0)
     const bool anch = jobs[0].mode == FWD_ANCHORED;
-    if ((e = fwd_init_launch(dprobs, np, hp.data(), 0, anch ? 0 : -sc.go, lane16, s)))
+    if ((e = fwd_init_launch(dprobs, np, hp.data(), 0, anch ? 0 : -sc.go, lane16 ? (rel && anch ? 2 : 1) : 0, s)))
         return set_cuda_error(ctx, e, "forward init");
     FwdParams P;
     std::memset(&P, 0, sizeof P);
@@ -270,6 +271,7 @@ static int run_forward_impl(sw_ctx *ctx, const SchemeDev &sc, const std::vector<
                 hp[0].gin ? ", bounded by the forward record" : "");
     }
     if (stats) {
+        stats->band_rows = R;
         if (jobs[0].mode == FWD_LOCAL) stats->fwd_cells += (int64_t)hst[0];
         stats->cells_computed += (int64_t)hst[0];
         stats->tiles_total += (int64_t)hst[1];
@@ -454,6 +456,9 @@ int sw_ctx_set_option(sw_ctx *ctx, int option, int64_t value)
     case SW_OPT_FORWARD_LANES:
         if (value != 0 && value != 16 && value != 32) return SW_EINVAL;
         ctx->opt.forward_lanes = (int)value; return SW_OK;
+    case SW_OPT_AUTOTUNE:
+        if (value != 0 && value != 1) return SW_EINVAL;
+        ctx->opt.autotune = (int)value; return SW_OK;
     case SW_OPT_TRACE:
         if (value != 0 && value != 1) return SW_EINVAL;
         ctx->opt.trace = (int)value; return SW_OK;

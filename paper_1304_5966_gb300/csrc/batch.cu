@@ -23,6 +23,16 @@ using namespace swgb;
 
 namespace swgb {
 
+// batch shape for the band-height table: pair count, mean and largest row
+// count, each rounded down to a power of two
+static uint64_t batch_shape_key(const std::vector<FwdJob> &jobs)
+{
+    int64_t sum = 0, mx = 0;
+    for (const FwdJob &j : jobs) { sum += j.n; mx = std::max<int64_t>(mx, j.n); }
+    auto lg = [](int64_t x) { uint64_t b = 0; while (x > 1) { x >>= 1; ++b; } return b; };
+    return lg((int64_t)jobs.size()) << 40 | lg(sum / (int64_t)jobs.size()) << 20 | lg(mx);
+}
+
 // can this pair run on int16x2 lanes without possible overflow?
 static bool fits_int16(const SchemeDev &sc, int64_t n, int64_t m)
 {
@@ -70,7 +80,39 @@ int batch_forward(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const uin
     if (!j16.empty()) {
         std::vector<int4> res;
         std::vector<int> ovf;
-        if ((st = run_forward16(ctx, sc, j16, prune, 0, res, ovf, stats, &ms))) return st;
+        // Band height of the int16x2 pass: taken from the context's table for this
+        // batch shape, or found by timing each candidate on this batch (every
+        // candidate gives the same results; the fastest run's are kept).
+        int rpt = 0;
+        bool timed = false;
+        if (ctx->opt.autotune && j16.size() > 1) {
+            const uint64_t key = batch_shape_key(j16);
+            auto it = ctx->tuned_rpt16.find(key);
+            if (it != ctx->tuned_rpt16.end()) {
+                rpt = it->second;
+            } else {
+                float best = 0;
+                sw_stats sbest{};
+                for (int cand : {4, 8, 16}) {
+                    std::vector<int4> r;
+                    std::vector<int> o;
+                    sw_stats sc_{};
+                    float ms_c = 0;
+                    if ((st = run_forward16(ctx, sc, j16, prune, cand, r, o, &sc_, &ms_c))) return st;
+                    if (!timed || ms_c < best) {
+                        best = ms_c; rpt = cand; res.swap(r); ovf.swap(o); sbest = sc_; timed = true;
+                    }
+                }
+                ctx->tuned_rpt16[key] = rpt;
+                ms = best;
+                if (stats) {
+                    stats->fwd_cells += sbest.fwd_cells; stats->cells_computed += sbest.cells_computed;
+                    stats->tiles_total += sbest.tiles_total; stats->tiles_pruned += sbest.tiles_pruned;
+                    stats->band_rows = sbest.band_rows; stats->tuned = 1;
+                }
+            }
+        }
+        if (!timed && (st = run_forward16(ctx, sc, j16, prune, rpt, res, ovf, stats, &ms))) return st;
         for (size_t k = 0; k < j16.size(); ++k) {
             if (ovf[k]) { j32.push_back(j16[k]); id32.push_back(id16[k]); if (stats) stats->int16_reruns++; }
             else store(id16[k], res[k]);
@@ -124,11 +166,13 @@ extern "C" int sw_align_batch(sw_ctx *ctx, const sw_pair *pairs, int32_t count, 
             if (la[p]) std::memcpy(hA.data() + aoff[p], pairs[p].a, (size_t)la[p]);
             if (lb[p]) std::memcpy(hB.data() + boff[p], pairs[p].b, (size_t)lb[p]);
         }
-        for (int64_t i = 0; i < ta; ++i) if (hA[i] >= sc.alphabet) { ctx->last_error = "sequence code >= alphabet"; return SW_EINVAL; }
-        for (int64_t i = 0; i < tb; ++i) if (hB[i] >= sc.alphabet) { ctx->last_error = "sequence code >= alphabet"; return SW_EINVAL; }
         if ((e = cudaMemcpyAsync(dA, hA.data(), (size_t)ta, cudaMemcpyHostToDevice, ctx->stream)) ||
             (e = cudaMemcpyAsync(dB, hB.data(), (size_t)tb, cudaMemcpyHostToDevice, ctx->stream)))
             return set_cuda_error(ctx, e, "batch upload");
+        // the code check runs on the device copies (one kernel per arena)
+        const uint8_t *chk;
+        if ((st = stage_seq(ctx, s, dA, ta, sc.alphabet, true, &chk))) return st;
+        if ((st = stage_seq(ctx, s, dB, tb, sc.alphabet, true, &chk))) return st;
     } else {
         for (int p = 0; p < count; ++p) {
             if ((la[p] && (e = cudaMemcpyAsync(dA + aoff[p], pairs[p].a, (size_t)la[p], cudaMemcpyDeviceToDevice, ctx->stream))) ||
@@ -159,6 +203,8 @@ extern "C" int sw_align_batch(sw_ctx *ctx, const sw_pair *pairs, int32_t count, 
     outs[0].stats.tiles_total = agg.tiles_total;
     outs[0].stats.tiles_pruned = agg.tiles_pruned;
     outs[0].stats.int16_reruns = agg.int16_reruns;
+    outs[0].stats.band_rows = agg.band_rows;
+    outs[0].stats.tuned = agg.tuned;
     if (!score_only) {
         const bool prune = !(flags & SW_FLAG_NO_PRUNE);
         // start points: one anchored launch over all reversed prefixes

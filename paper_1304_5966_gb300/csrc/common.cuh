@@ -82,22 +82,39 @@ __device__ __forceinline__ int wait_flag(const int *flag, int need, int *err,
     }
 }
 
-// Self-validating boundary-row entry (int16x2 kernel): H as int32, how far F
-// lies below H (clamped at 0xffff: farther below, F - ge stays under H - go for
-// any gap open up to 0xffff, so F no longer matters), and the tag of the band
-// that wrote it, ((band & 0x7fff) << 1) | useful.  One 64-bit word, read and
-// written whole, so a reader that finds its predecessor's tag has its data.
-__host__ __device__ __forceinline__ unsigned bus_tag(int band, bool useful) {
-    return ((unsigned)band & 0x7fffu) << 1 | (useful ? 1u : 0u);
-}
-__host__ __device__ __forceinline__ unsigned long long busw_pack(int h, int f, unsigned tag) {
-    const long long d = (long long)h - f;
-    const unsigned dd = d > 0xffff ? 0xffffu : (unsigned)d;
-    return (unsigned long long)(unsigned)h | ((unsigned long long)dd << 32) | ((unsigned long long)(tag & 0xffffu) << 48);
-}
-__device__ __forceinline__ int busw_h(unsigned long long w) { return (int)(unsigned)(w & 0xffffffffull); }
-__device__ __forceinline__ int busw_f(unsigned long long w) { return busw_h(w) - (int)((w >> 32) & 0xffffu); }
-__device__ __forceinline__ unsigned busw_tag(unsigned long long w) { return (unsigned)(w >> 48); }
+// Self-validating boundary-row entry (int16x2 kernel): one 64-bit word per
+// column, read and written whole, so a reader that finds its predecessor's tag
+// has its data.  Bits 0-31 hold H as int32; then how far F lies below H, D bits
+// clamped at 2^D - 1 (exact while go - ge < 2^D: farther below, F - ge stays
+// under H - go, so F no longer matters); then the tag of the band that wrote
+// it, (band mod P) << 1 | useful, where P = 2^(31 - D) - 1 and the all-ones
+// band field P is reserved for row 0 (only band 0 reads it).
+//  * WIDE = false (D = 16, P = 32767): the local passes, whose bands write
+//    every column of the row, so a reader never meets a word older than its
+//    predecessor's.
+//  * WIDE = true (D = 8, P = 2^23 - 1): the anchored passes, whose bands write
+//    only their live range, so a column can keep a word from any earlier band.
+//    Their schemes have go - ge <= 255, and a band index stays below P (at
+//    least 256 rows a band and fewer than 2^31 rows), so no two bands share a
+//    tag.
+template <bool WIDE> struct BusWord {
+    static constexpr int DBITS = WIDE ? 8 : 16;
+    static constexpr unsigned DMAX = (1u << DBITS) - 1u;
+    static constexpr int TSHIFT = 32 + DBITS;
+    static constexpr unsigned ROW0 = (1u << (31 - DBITS)) - 1u;   // reserved band field
+    __host__ __device__ static unsigned band_tag(int band) {
+        return band < 0 ? ROW0 : (unsigned)band % ROW0;
+    }
+    __host__ __device__ static unsigned tag(int band, bool useful) { return band_tag(band) << 1 | (useful ? 1u : 0u); }
+    __host__ __device__ static unsigned long long pack(int h, int f, unsigned t) {
+        const long long d = (long long)h - f;
+        const unsigned dd = d > (long long)DMAX ? DMAX : (unsigned)d;
+        return (unsigned long long)(unsigned)h | ((unsigned long long)dd << 32) | ((unsigned long long)t << TSHIFT);
+    }
+    __device__ static int h(unsigned long long w) { return (int)(unsigned)(w & 0xffffffffull); }
+    __device__ static int f(unsigned long long w) { return h(w) - (int)((w >> 32) & DMAX); }
+    __device__ static unsigned tag_of(unsigned long long w) { return (unsigned)(w >> TSHIFT); }
+};
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
     unsigned long long v;
     asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");

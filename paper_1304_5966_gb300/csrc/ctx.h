@@ -110,6 +110,7 @@ struct Options {
     int64_t leaf_cells = 1 << 16;
     int forward_lanes = 0;         // 0 auto, 16 int16x2 (offset) lanes, 32 int32 lanes
     int trace = 0;                 // 1: one stderr line per device pass
+    int autotune = 1;              // 1: batch band height timed per batch shape
 };
 
 }  // namespace swgb
@@ -127,6 +128,7 @@ struct sw_ctx {
     cudaEvent_t ev[10] = {};
     std::mutex call_mu;
     int64_t launches = 0;          // kernels launched by this context (all calls)
+    std::map<uint64_t, int> tuned_rpt16;   // batch shape -> fastest int16x2 band height
 };
 
 namespace swgb {

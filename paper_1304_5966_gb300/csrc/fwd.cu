@@ -283,9 +283,10 @@ __global__ void fwd_init_kernel(FwdProblem *probs, int nprobs, int h0, int f0, i
     if (p >= nprobs) return;
     FwdProblem pr = probs[p];
     // row 0: {H, F} pairs (int32 lanes) or self-validating words tagged as
-    // written by band -1 (int16x2 lanes)
+    // written by band -1 (int16x2 lanes; packed 2: the anchored passes' layout)
     if (packed) {
-        const unsigned long long w = busw_pack(h0, f0, bus_tag(-1, true));
+        const unsigned long long w = packed == 2 ? BusWord<true>::pack(h0, f0, BusWord<true>::tag(-1, true))
+                                                 : BusWord<false>::pack(h0, f0, BusWord<false>::tag(-1, true));
         for (int j = threadIdx.x; j < pr.m; j += blockDim.x) ((unsigned long long *)pr.bus)[j] = w;
     } else {
         for (int j = threadIdx.x; j < pr.m; j += blockDim.x) pr.bus[j] = make_int2(h0, f0);
@@ -376,11 +377,11 @@ cudaError_t fwd_occupancy(int rpt, bool p2, int threads, int *n)
     }
 }
 
-cudaError_t fwd_init_launch(FwdProblem *probs_dev, int nprobs, const FwdProblem *, int h0, int f0, bool packed,
+cudaError_t fwd_init_launch(FwdProblem *probs_dev, int nprobs, const FwdProblem *, int h0, int f0, int packed,
                             cudaStream_t s)
 {
     if (nprobs <= 0) return cudaSuccess;
-    fwd_init_kernel<<<nprobs, 256, 0, s>>>(probs_dev, nprobs, h0, f0, packed ? 1 : 0);
+    fwd_init_kernel<<<nprobs, 256, 0, s>>>(probs_dev, nprobs, h0, f0, packed);
     return cudaGetLastError();
 }
 

@@ -173,7 +173,8 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
         const uint8_t *__restrict__ bseq = pr.b;
         unsigned long long *__restrict__ busw = (unsigned long long *)pr.bus;
         int *stop = anch ? pr.stop_band : nullptr;
-        const unsigned want_tag = (unsigned)(band - 1) & 0x7fffu;   // tag of the row above
+        using BW = BusWord<anch>;
+        const unsigned want_tag = BW::band_tag(band - 1);           // tag of the row above
         const int guard = 32767 - P.max_sub;
         const int target = pr.target;
         // dead values of skipped cells, absolute (what the boundary row carries)
@@ -277,11 +278,11 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
             bool ok = true;
             if (col < m) {
                 w = ld_relaxed_u64(&busw[col]);
-                ok = (busw_tag(w) >> 1) == want_tag;
+                ok = (BW::tag_of(w) >> 1) == want_tag;
             }
             if (__all_sync(FULL, ok)) {
-                v = make_int2(busw_h(w), busw_f(w));
-                return __shfl_sync(FULL, (int)(busw_tag(w) & 1u), 0);   // column c * CH < m
+                v = make_int2(BW::h(w), BW::f(w));
+                return __shfl_sync(FULL, (int)(BW::tag_of(w) & 1u), 0);   // column c * CH < m
             }
             if (pred_last) {
                 int y = 0;
@@ -682,10 +683,10 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
             }
             if (has_next) {
                 if (from_bus) {
-                    const bool ok = ncol >= m || (busw_tag(wnext) >> 1) == want_tag;
+                    const bool ok = ncol >= m || (BW::tag_of(wnext) >> 1) == want_tag;
                     if (__all_sync(FULL, ok)) {
-                        nst = __shfl_sync(FULL, (int)(busw_tag(wnext) & 1u), 0);
-                        if (nst == 1 && ncol < m) nv = make_int2(busw_h(wnext), busw_f(wnext));
+                        nst = __shfl_sync(FULL, (int)(BW::tag_of(wnext) & 1u), 0);
+                        if (nst == 1 && ncol < m) nv = make_int2(BW::h(wnext), BW::f(wnext));
                     }
                 }
                 if (nst == 2) {
@@ -757,7 +758,7 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                     // one self-validating word per column (a band that never
                     // publishes, for testing, writes nothing)
                     if (col < m && band != P.fault_band)
-                        st_relaxed_u64(&busw[col], busw_pack(outv.x, outv.y, bus_tag(band, useful)));
+                        st_relaxed_u64(&busw[col], BW::pack(outv.x, outv.y, BW::tag(band, useful)));
                     __syncwarp();
                     if (lane == 0 && band != P.fault_band && dyn && useful && !first_pub)
                         st_release(&pr.span[band].x, c);

@@ -73,9 +73,10 @@ cudaError_t fwd_launch(const FwdParams &p, int rpt, bool two_word_profile, int c
                        int threads, cudaStream_t s);
 cudaError_t fwd_occupancy(int rpt, bool two_word_profile, int threads, int *ctas_per_sm);
 // fills bus with {h0, f0} and flags with -1 etc. for a set of problems
-// packed: the boundary row holds the int16x2 kernel's self-validating words
+// packed: 0 for {H, F} pairs (int32 lanes); the int16x2 kernel's
+// self-validating words in the local (1) or anchored (2) layout (BusWord)
 cudaError_t fwd_init_launch(FwdProblem *probs_dev, int nprobs, const FwdProblem *probs_host,
-                            int h0, int f0, bool packed, cudaStream_t s);
+                            int h0, int f0, int packed, cudaStream_t s);
 // per-problem reduction of band results -> out[p] = {score, row, col, found}
 cudaError_t fwd_reduce_launch(const FwdProblem *probs_dev, int nprobs, int4 *out,
                               cudaStream_t s);

@@ -152,3 +152,28 @@ def test_batch_4096_golden(sw, ctx):
     got = sw.sw_align_batch(ctx, pairs, flags=sw.SW_FLAG_SCORE_ONLY)
     want = [tuple(x) if x[0] else (0, -1, -1) for x in g["score_end"]]
     assert [_se(r) for r in got] == want
+
+
+def test_band_height_tuning(sw):
+    """The first batch of a shape times each int16x2 band height and keeps the
+    fastest for that shape; tuned, cached and untuned calls return the same
+    (oracle-equal) results."""
+    c = sw.sw_ctx_create(0, workspace_bytes=2 << 30)
+    try:
+        pairs = _mixed_pairs(64, seed=71, lo=200, hi=2500)
+        want = []
+        for a, b in pairs:
+            S, ei, ej = oracle.local_score(a, b)
+            want.append((S, ei, ej) if S else (0, -1, -1))
+        first = sw.sw_align_batch(c, pairs, flags=sw.SW_FLAG_SCORE_ONLY)
+        again = sw.sw_align_batch(c, pairs, flags=sw.SW_FLAG_SCORE_ONLY)
+        c.set_option(sw.SW_OPT_AUTOTUNE, 0)
+        plain = sw.sw_align_batch(c, pairs, flags=sw.SW_FLAG_SCORE_ONLY)
+        assert first[0].stats["tuned"] == 1 and again[0].stats["tuned"] == 0 and plain[0].stats["tuned"] == 0
+        assert first[0].stats["band_rows"] in (256, 512, 1024)
+        assert again[0].stats["band_rows"] == first[0].stats["band_rows"]
+        for k, (a, b) in enumerate(pairs):
+            got = [_se(r[k]) for r in (first, again, plain)]
+            assert got[0] == got[1] == got[2] == want[k], k
+    finally:
+        c.close()
