@@ -95,6 +95,8 @@ typedef struct {
     int64_t align_cells;       /* cells computed by the reconstruction label passes */
     int32_t band_rows;         /* rows per band of the forward pass (int16x2 batch: as tuned) */
     int32_t tuned;             /* batch: 1 when this call timed the candidate band heights */
+    int32_t cta_warps;         /* warps per CTA of the local forward pass: 4, or 12-20 when one
+                                  CTA per SM runs consecutive bands on each scheduler */
 } sw_stats;
 
 typedef struct {

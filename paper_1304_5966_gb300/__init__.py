@@ -53,7 +53,8 @@ class _Stats(ctypes.Structure):
                 ("ms_forward", ctypes.c_float), ("ms_start", ctypes.c_float),
                 ("ms_align", ctypes.c_float), ("fwd_cells", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("start_cells", ctypes.c_int64),
-                ("align_cells", ctypes.c_int64), ("band_rows", ctypes.c_int32), ("tuned", ctypes.c_int32)]
+                ("align_cells", ctypes.c_int64), ("band_rows", ctypes.c_int32), ("tuned", ctypes.c_int32),
+                ("cta_warps", ctypes.c_int32)]
 
 
 class _Result(ctypes.Structure):

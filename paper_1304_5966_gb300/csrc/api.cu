@@ -109,7 +109,7 @@ static int auto_rpt16(sw_ctx *ctx, const std::vector<FwdJob> &jobs, bool rel, co
     for (int k = 0; k < 3; ++k) {
         if (rel && !rel16_fits(sc, cands[k])) continue;
         int per_sm = 1;
-        if (fwd16_occupancy(cands[k], rel, rel && jobs[0].mode == FWD_ANCHORED, &per_sm) != cudaSuccess ||
+        if (fwd16_occupancy(cands[k], rel, rel && jobs[0].mode == FWD_ANCHORED, false, &per_sm) != cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
         const double warps = 4.0 * per_sm * ctx->sms;
@@ -232,18 +232,23 @@ static int run_forward_impl(sw_ctx *ctx, const SchemeDev &sc, const std::vector<
     P.fault_band = ctx->opt.fault_band;
     P.timeout_ns = (unsigned long long)ctx->opt.timeout_ms * 1000000ull;
     const bool p2 = sc.alphabet > 4;
-    int ctas;
+    int ctas, cta_warps = 4;
+    // local pass with offset lanes and bands enough to fill every SM twice over:
+    // one CTA per SM, each scheduler on consecutive bands
+    const bool wide = lane16 && rel && !anch && ctx->opt.warps_per_sm <= 0 &&
+                      ntk >= 2 * (int64_t)ctx->sms * fwd16_cta_warps(rpt, true);
     if (lane16) {
         int per_sm = 1;
-        if (fwd16_occupancy(rpt, rel, rel && anch, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+        cta_warps = fwd16_cta_warps(rpt, wide);
+        if (fwd16_occupancy(rpt, rel, rel && anch, wide, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
         if (ctx->opt.warps_per_sm > 0) per_sm = std::max(1, std::min(per_sm, ctx->opt.warps_per_sm / 4));
         ctas = per_sm * ctx->sms;
     } else {
         ctas = occupancy_ctas(ctx, rpt, p2);
     }
-    ctas = (int)std::min<int64_t>(ctas, (ntk + 3) / 4);
+    ctas = (int)std::min<int64_t>(ctas, (ntk + cta_warps - 1) / cta_warps);
     cudaEventRecord(ctx->ev[0], s);
-    if ((e = lane16 ? fwd16_launch(P, rpt, rel, rel && anch, ctas, s) : fwd_launch(P, rpt, p2, ctas, 128, s)))
+    if ((e = lane16 ? fwd16_launch(P, rpt, rel, rel && anch, wide, ctas, s) : fwd_launch(P, rpt, p2, ctas, 128, s)))
         return set_cuda_error(ctx, e, "forward launch");
     cudaEventRecord(ctx->ev[1], s);
     if ((e = fwd_reduce_launch(dprobs, np, dres, s))) return set_cuda_error(ctx, e, "forward reduce");
@@ -265,14 +270,14 @@ static int run_forward_impl(sw_ctx *ctx, const SchemeDev &sc, const std::vector<
     if (ctx->opt.trace) {
         float kms = 0;
         cudaEventElapsedTime(&kms, ctx->ev[0], ctx->ev[1]);
-        fprintf(stderr, "swgb: %s pass: %d problem(s), %s lanes, %d rows/band, %.2f ms, cells %.4g, chunks %llu pruned %llu%s%s\n",
-                anch ? "anchored" : "local", np, lane16 ? (rel ? "int16x2 offset" : "int16x2") : "int32", R, kms,
+        fprintf(stderr, "swgb: %s pass: %d problem(s), %s lanes, %d rows/band, %d warps/CTA, %.2f ms, cells %.4g, chunks %llu pruned %llu%s%s\n",
+                anch ? "anchored" : "local", np, lane16 ? (rel ? "int16x2 offset" : "int16x2") : "int32", R, cta_warps, kms,
                 (double)hst[0], hst[1], hst[2], hp[0].gout ? ", recording rows" : "",
                 hp[0].gin ? ", bounded by the forward record" : "");
     }
     if (stats) {
         stats->band_rows = R;
-        if (jobs[0].mode == FWD_LOCAL) stats->fwd_cells += (int64_t)hst[0];
+        if (jobs[0].mode == FWD_LOCAL) { stats->fwd_cells += (int64_t)hst[0]; stats->cta_warps = cta_warps; }
         stats->cells_computed += (int64_t)hst[0];
         stats->tiles_total += (int64_t)hst[1];
         stats->tiles_pruned += (int64_t)hst[2];

@@ -55,6 +55,19 @@ constexpr uint32_t SEL_NEUTRAL = (0u | (8u << 4)) | (((0u | (8u << 4)) + 0x44u) 
 // per-halfword max of two (DPX three-input form with a repeated operand)
 __device__ __forceinline__ uint32_t vmax16(uint32_t a, uint32_t b) { return __vimax3_s16x2(a, b, b); }
 
+// A step's detection value: max(thr1, H of every row of the lane) per half,
+// in three-way maxima over pairs of rows (RPT / 2 operations), so it differs
+// from thr1 exactly when some cell of the step exceeds the threshold.
+template <int RPT>
+__device__ __forceinline__ uint32_t rows_max(const uint32_t (&Hl)[RPT], uint32_t thr1)
+{
+    uint32_t m = __vimax3_s16x2(thr1, Hl[0], Hl[RPT > 1 ? 1 : 0]);
+#pragma unroll
+    for (int k = 2; k + 1 < RPT; k += 2) m = __vimax3_s16x2(m, Hl[k], Hl[k + 1]);
+    if (RPT > 2 && (RPT & 1)) m = vmax16(m, Hl[RPT - 1]);
+    return m;
+}
+
 constexpr int REL_FLOOR = -32768 + 256;
 constexpr int REL_TOP = 16384;
 
@@ -113,11 +126,19 @@ __device__ __forceinline__ int32_t *rec_row(const FwdProblem &pr, int band)
     return pr.gout + (size_t)((band + 1) / pr.gstride - 1) * (size_t)(pr.gnch + 2);
 }
 
-template <int RPT, bool REL, bool ANCH>
-__global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
+template <int RPT, bool REL, bool ANCH, int NW>
+__global__ void __launch_bounds__(NW * 32) fwd16_kernel(const FwdParams P)
 {
-    __shared__ int4 s_in_all[4][3][CH];   // {H, F, selector8, 0} per column, three chunks
-    __shared__ uint32_t s_out_all[4][2 * CH];   // bottom row, packed int16 (H | F << 16)
+    // NW warps per CTA.  Four: every warp claims its own band.  More (one CTA
+    // per SM, the full-width local pass): the CTA claims NW consecutive bands
+    // and gives each scheduler (warp slots s, s + 4, s + 8, ...) NW / 4
+    // consecutive ones, slot order = band order.  A scheduler favours its
+    // older warps; with bands of unrelated parts of the chain on one
+    // scheduler, the band that loses holds up every band after it, while here
+    // the favoured warp is the one the others wait for.
+    static_assert(NW % 4 == 0 && (NW == 4 || !ANCH), "grouped hand-over uses four-warp CTAs");
+    __shared__ int4 s_in_all[NW][3][CH];   // {H, F, selector8, 0} per column, three chunks
+    __shared__ uint32_t s_out_all[NW][2 * CH];   // bottom row, packed int16 (H | F << 16)
     // Grouped launch (anchored): a CTA takes four consecutive tickets, and a band
     // whose successor runs in the same CTA hands its bottom row over through a
     // ring of GK chunks in shared memory instead of the boundary row in HBM and
@@ -130,8 +151,8 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
     __shared__ int s_tag[GROUP ? GW : 1][GROUP ? GK : 1];         // 2 * chunk + useful
     __shared__ int s_need[GW], s_spx[GW], s_spy[GW];              // reader's next chunk; span
     __shared__ int s_base, s_err;
-    __shared__ int s_grun[4];                                     // record row's running maximum
-    __shared__ int32_t *s_grow[4];                                // record row of the warp's band
+    __shared__ int s_grun[NW];                                    // record row's running maximum
+    __shared__ int32_t *s_grow[NW];                               // record row of the warp's band
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     int4 (*s_in)[CH] = s_in_all[wid];
@@ -157,6 +178,14 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
             gbase = s_base;
             if (gbase >= P.ntickets || s_err) return;      // the whole CTA leaves together
             tk = gbase + wid;
+            if (tk >= P.ntickets) continue;
+        } else if (NW > 4) {
+            __syncthreads();                               // the previous claim is done
+            if (threadIdx.x == 0) { s_base = atomicAdd(P.ticket_ctr, NW); s_err = ld_volatile(P.err); }
+            __syncthreads();
+            gbase = s_base;
+            if (gbase >= P.ntickets || s_err) return;      // the whole CTA leaves together
+            tk = gbase + (wid & 3) * (NW / 4) + (wid >> 2);
             if (tk >= P.ntickets) continue;
         } else {
             if (lane == 0) { tk = atomicAdd(P.ticket_ctr, 1); stop_now = ld_volatile(P.err); }
@@ -557,7 +586,6 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                     updiag = upH;
                     uint32_t hgo = __viaddmax_s16x2(upH, go2, NEG2);       // H(i-1, j) - go
                     uint32_t F = upF;
-                    uint32_t smax = REL ? NEG2 : ZERO2;
 #pragma unroll
                     for (int k = 0; k < RPT; ++k) {
                         const uint32_t sc = perm(plo[k], phi[k], sel);
@@ -569,11 +597,11 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                         Hl[k] = h;
                         hgo = __viaddmax_s16x2(h, go2, NEG2);
                         E[k] = __viaddmax_s16x2(E[k], ge2, hgo);               // E(i, j+1)
-                        smax = vmax16(smax, h);                                // running maximum
                     }
                     Hlast = Hl[RPT - 1];
                     Flast = F;
-                    if (vmax16(smax, thr1) != thr1) {
+                    const uint32_t smax = rows_max<RPT>(Hl, thr1);
+                    if (smax != thr1) {
                         const bool pl = lo16(smax) > lo16(thr1), ph = hi16(smax) > hi16(thr1);
                         const int jlo = s - lane, jhi = s - lane - 32;
                         const int sl = lo16(smax) + O, sh = hi16(smax) + O;
@@ -623,7 +651,7 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                         const uint32_t oFlast = Flast;
                         uint32_t hgo = __viaddmax_s16x2(upH, go2, NEG2);   // H(i-1, j) - go
                         uint32_t F = upF;
-                        uint32_t smax = REL ? NEG2 : ZERO2;
+                        uint32_t smax;
                         if (!partial) {
 #pragma unroll
                             for (int k = 0; k < RPT; ++k) {
@@ -636,8 +664,8 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                                 Hl[k] = h;
                                 hgo = __viaddmax_s16x2(h, go2, NEG2);
                                 E[k] = __viaddmax_s16x2(E[k], ge2, hgo);               // E(i, j+1)
-                                smax = REL ? vmax16(smax, h) : __vimax_s16x2_relu(smax, h);
                             }
+                            smax = rows_max<RPT>(Hl, thr1);
                             Hlast = Hl[RPT - 1];
                             Flast = F;
                         } else {
@@ -652,13 +680,13 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
                                 Hl[k] = perm(h, Hl[k], ks);
                                 hgo = __viaddmax_s16x2(h, go2, NEG2);
                                 E[k] = perm(__viaddmax_s16x2(E[k], ge2, hgo), E[k], ks);
-                                smax = REL ? vmax16(smax, h) : __vimax_s16x2_relu(smax, h);
                             }
-                            smax = perm(smax, REL ? NEG2 : 0u, ks);
+                            // the half outside the matrix keeps older values: it takes thr1
+                            smax = perm(rows_max<RPT>(Hl, thr1), thr1, ks);
                             Hlast = Hl[RPT - 1];
                             Flast = perm(F, oFlast, ks);
                         }
-                        if (vmax16(smax, thr1) != thr1) {
+                        if (smax != thr1) {
                             const bool pl = lo16(smax) > lo16(thr1), ph = hi16(smax) > hi16(thr1);
                             const int sl = lo16(smax) + O, sh = hi16(smax) + O;
                             if (pl && vlo) {
@@ -845,46 +873,55 @@ __global__ void __launch_bounds__(128) fwd16_kernel(const FwdParams P)
     }
 }
 
-template <int RPT, bool REL, bool ANCH>
+// warps per CTA of the one-CTA-per-SM layout: what the registers of each
+// band height allow on one SM
+static constexpr int wide_warps(int rpt) { return rpt == 16 ? 12 : rpt == 8 ? 16 : 20; }
+
+int fwd16_cta_warps(int rpt, bool wide) { return wide ? wide_warps(rpt) : 4; }
+
+template <int RPT, bool REL, bool ANCH, int NW>
 static cudaError_t launch16(const FwdParams &p, int ctas, cudaStream_t s)
 {
-    fwd16_kernel<RPT, REL, ANCH><<<ctas, 128, 0, s>>>(p);
+    fwd16_kernel<RPT, REL, ANCH, NW><<<ctas, NW * 32, 0, s>>>(p);
     return cudaGetLastError();
 }
 
 template <int RPT>
-static cudaError_t launch16_rpt(const FwdParams &p, bool rel, bool anch, int ctas, cudaStream_t s)
+static cudaError_t launch16_rpt(const FwdParams &p, bool rel, bool anch, bool wide, int ctas, cudaStream_t s)
 {
-    if (!rel) return anch ? cudaErrorInvalidValue : launch16<RPT, false, false>(p, ctas, s);
-    return anch ? launch16<RPT, true, true>(p, ctas, s) : launch16<RPT, true, false>(p, ctas, s);
+    if (!rel) return anch ? cudaErrorInvalidValue : launch16<RPT, false, false, 4>(p, ctas, s);
+    if (anch) return launch16<RPT, true, true, 4>(p, ctas, s);
+    return wide ? launch16<RPT, true, false, wide_warps(RPT)>(p, ctas, s) : launch16<RPT, true, false, 4>(p, ctas, s);
 }
 
 template <int RPT>
-static cudaError_t occupancy16_rpt(bool rel, bool anch, int *n)
+static cudaError_t occupancy16_rpt(bool rel, bool anch, bool wide, int *n)
 {
-    if (!rel) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<RPT, false, false>, 128, 0);
-    return anch ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<RPT, true, true>, 128, 0)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<RPT, true, false>, 128, 0);
+    if (!rel) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<RPT, false, false, 4>, 128, 0);
+    if (anch) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<RPT, true, true, 4>, 128, 0);
+    return wide ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<RPT, true, false, wide_warps(RPT)>,
+                                                                wide_warps(RPT) * 32, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, fwd16_kernel<RPT, true, false, 4>, 128, 0);
 }
 
 bool fwd16_rpt_supported(int rpt) { return rpt == 4 || rpt == 8 || rpt == 16; }
 
-cudaError_t fwd16_launch(const FwdParams &p, int rpt, bool rel, bool anch, int ctas, cudaStream_t s)
+cudaError_t fwd16_launch(const FwdParams &p, int rpt, bool rel, bool anch, bool wide, int ctas, cudaStream_t s)
 {
     switch (rpt) {
-    case 4: return launch16_rpt<4>(p, rel, anch, ctas, s);
-    case 8: return launch16_rpt<8>(p, rel, anch, ctas, s);
-    case 16: return launch16_rpt<16>(p, rel, anch, ctas, s);
+    case 4: return launch16_rpt<4>(p, rel, anch, wide, ctas, s);
+    case 8: return launch16_rpt<8>(p, rel, anch, wide, ctas, s);
+    case 16: return launch16_rpt<16>(p, rel, anch, wide, ctas, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t fwd16_occupancy(int rpt, bool rel, bool anch, int *n)
+cudaError_t fwd16_occupancy(int rpt, bool rel, bool anch, bool wide, int *n)
 {
     switch (rpt) {
-    case 4: return occupancy16_rpt<4>(rel, anch, n);
-    case 8: return occupancy16_rpt<8>(rel, anch, n);
-    case 16: return occupancy16_rpt<16>(rel, anch, n);
+    case 4: return occupancy16_rpt<4>(rel, anch, wide, n);
+    case 8: return occupancy16_rpt<8>(rel, anch, wide, n);
+    case 16: return occupancy16_rpt<16>(rel, anch, wide, n);
     default: return cudaErrorInvalidValue;
     }
 }

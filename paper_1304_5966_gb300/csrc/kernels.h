@@ -67,8 +67,11 @@ bool fwd_rpt_supported(int rpt);
 bool fwd16_rpt_supported(int rpt);
 // rel: values relative to a per-warp offset (long pairs, local and anchored modes)
 // anch: every problem of the launch is anchored (offset lanes only)
-cudaError_t fwd16_launch(const FwdParams &p, int rpt, bool rel, bool anch, int ctas, cudaStream_t s);
-cudaError_t fwd16_occupancy(int rpt, bool rel, bool anch, int *ctas_per_sm);
+// wide: one CTA per SM whose schedulers each run consecutive bands (local mode
+// with offset lanes only); fwd16_cta_warps gives its warps per CTA
+cudaError_t fwd16_launch(const FwdParams &p, int rpt, bool rel, bool anch, bool wide, int ctas, cudaStream_t s);
+cudaError_t fwd16_occupancy(int rpt, bool rel, bool anch, bool wide, int *ctas_per_sm);
+int fwd16_cta_warps(int rpt, bool wide);
 cudaError_t fwd_launch(const FwdParams &p, int rpt, bool two_word_profile, int ctas,
                        int threads, cudaStream_t s);
 cudaError_t fwd_occupancy(int rpt, bool two_word_profile, int threads, int *ctas_per_sm);

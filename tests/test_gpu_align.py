@@ -204,3 +204,27 @@ def test_offset_lanes_band_heights(sw, ctx, rpt):
     finally:
         ctx.set_option(sw.SW_OPT_FORWARD_LANES, 0)
         ctx.set_option(sw.SW_OPT_ROWS_PER_THREAD, 0)
+
+
+def test_local_pass_one_cta_per_sm(sw, ctx):
+    """A local pass with bands enough for the one-CTA-per-SM layout (each
+    scheduler on consecutive bands, 256-row bands): score and end equal the
+    oracle's, pruning on and off, and the layout was the one used."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 2 * sms * 20 * 256 + 70_001           # past the layout's threshold, ragged last band
+    st = synth.Rng(97).stream()
+    a = synth.random_bases(st, n)
+    core = a[n - 300_000:n - 299_400].copy()
+    b = np.concatenate([synth.random_bases(st, 50), synth.mutate(st, core), synth.random_bases(st, 40)])
+    want = oracle.local_score(a, b)           # (score, a_end, b_end); the planted copy scores far above 0
+    ctx.set_option(sw.SW_OPT_FORWARD_LANES, 16)
+    ctx.set_option(sw.SW_OPT_ROWS_PER_THREAD, 4)
+    try:
+        for fl in (0, sw.SW_FLAG_NO_PRUNE):
+            r = sw.sw_score(ctx, a, b, flags=fl)
+            assert r.stats["cta_warps"] == 20
+            assert (r.score, r.a_end, r.b_end) == want
+    finally:
+        ctx.set_option(sw.SW_OPT_FORWARD_LANES, 0)
+        ctx.set_option(sw.SW_OPT_ROWS_PER_THREAD, 0)
