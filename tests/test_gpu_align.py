@@ -228,3 +228,45 @@ def test_local_pass_one_cta_per_sm(sw, ctx):
     finally:
         ctx.set_option(sw.SW_OPT_FORWARD_LANES, 0)
         ctx.set_option(sw.SW_OPT_ROWS_PER_THREAD, 0)
+
+
+def test_pair_5m_full_size():
+    """The 5,000,000 x 4,948,987 pair in the benchmark's launch configuration
+    (24 GiB workspace, default options).  The oracle cannot run the whole
+    matrix, so the checks are the ones that hold at any size plus sampled
+    sub-problems it solves one by one:
+      * pruning on and off give the same score and end point;
+      * the CIGAR rescored on the CPU equals the score and consumes exactly
+        [a_begin, a_end) x [b_begin, b_end), beginning and ending with a match;
+      * windows of the path between two nodes in state H are exactly the
+        oracle's greedy traceback of that sub-problem (the sub-path property
+        that test_oracle pins on exhaustive cases)."""
+    import paper_1304_5966_gb300 as sw
+    import torch
+    a, b = synth.pair_5m()
+    c = sw.sw_ctx_create(0, workspace_bytes=24 << 30)
+    try:
+        ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+        r = sw.sw_align(c, ta, tb)
+        rn = sw.sw_score(c, ta, tb, flags=sw.SW_FLAG_NO_PRUNE)
+    finally:
+        c.close()
+    assert r.score > 1_000_000
+    assert (rn.score, rn.a_end, rn.b_end) == (r.score, r.a_end, r.b_end)
+    ops = oracle.cigar_to_ops(r.cigar)
+    asub, bsub = a[r.a_begin:r.a_end], b[r.b_begin:r.b_end]
+    assert oracle.rescore(asub, bsub, ops) == (r.score, len(asub), len(bsub))
+    assert r.cigar.endswith("=") and r.cigar[:r.cigar.index("=")].isdigit()
+    # positions (i, j) before each op; a node after an 'M' op is in state H
+    steps = np.frombuffer(ops.encode(), dtype=np.uint8)
+    di = np.concatenate([[0], np.cumsum((steps == ord("M")) | (steps == ord("I")))])
+    dj = np.concatenate([[0], np.cumsum((steps == ord("M")) | (steps == ord("D")))])
+    h_nodes = np.flatnonzero(steps == ord("M")) + 1           # op index just after an 'M'
+    st = synth.Rng(5005).stream()
+    for _ in range(24):
+        k0 = int(h_nodes[st.int(0, len(h_nodes) - 1)])
+        k1 = int(h_nodes[np.searchsorted(h_nodes, min(k0 + st.int(500, 4000), int(h_nodes[-1])))])
+        if k1 <= k0:
+            continue
+        i0, j0, i1, j1 = int(di[k0]), int(dj[k0]), int(di[k1]), int(dj[k1])
+        assert oracle.verify_path(asub[i0:i1], bsub[j0:j1], ops[k0:k1]) == 0, (k0, k1)
