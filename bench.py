@@ -87,6 +87,33 @@ def run_profile_case(args):
                       "tiles_total": r.stats["tiles_total"]}), flush=True)
 
 
+def _config(n: int, m: int, world: int) -> dict:
+    """The workload both arms report (ours and the oracle's)."""
+    return {"workload": f"pair_5m: {n} x {m} DNA pair (GC 41%, tandem repeats, 10% subst, 1% ins, "
+                        f"1% del, 20 kbp inversion, 50 kbp deletion); sw_align = score + end, "
+                        f"start, CIGAR; match +1, mismatch -3, gap 5 + 2(k-1)",
+            "l2": "flushed before every step (256 MiB write); step working set < L2",
+            "arithmetic": "exact integer scores: forward and start passes on int16x2 DPX lanes with "
+                          "per-warp offsets, int32 boundary rows and reconstruction",
+            "parallelism": f"replicas x{world}"}
+
+
+def _max_over_ranks(dist, x: float, device: str) -> float:
+    """The largest x over all ranks (every rank gets it); x itself without a
+    process group.  The job's time is the slowest replica's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_gcups(world: int, cells: int, steps: int, total_s: float) -> float:
+    """Whole-job GCUPS: every replica aligns the pair `steps` times."""
+    return world * cells * steps / total_s / 1e9
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -169,7 +196,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": "GCUPS", "value": v, "unit": "GCUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": "pair_5m (oracle on a 40k x 40k prefix sample)"},
+            "config": _config(len(a), len(b), args.gpus),
             "cpu_baseline": {"value": v, "unit": "GCUPS", "cores": 1, "kind": "oracle", "sample": cb["sample"]},
             "e2e": {"value": v, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -215,7 +242,29 @@ def bench_batch(sw, ctx, reps: int = 3):
                     "single-pair path timed on every 16th pair, plain path on every 256th"}
 
 
-def bench_serving(sw, ctx, rates=(10.0, 100.0), count: int = 40):
+def bench_small_pairs(sw, ctx, reps: int = 9):
+    """The 1 kbp pair (BASELINE config 1) and the 100 kbp pair (config 2):
+    median wall latency of sw_align and of sw_score per call (host inputs,
+    results read back), and their GCUPS."""
+    from gen import synth
+    out = {}
+    for name, (a, b) in (("pair_1k", synth.pair_1k()), ("pair_100k", synth.pair_100k())):
+        row = {"n": len(a), "m": len(b)}
+        for fn in ("sw_score", "sw_align"):
+            f = getattr(sw, fn)
+            f(ctx, a, b)                                   # warm-up
+            ts = []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                r = f(ctx, a, b)
+                ts.append(time.perf_counter() - t0)
+            t = statistics.median(ts)
+            row[fn] = {"ms": round(t * 1e3, 3), "gcups": round(len(a) * len(b) / t / 1e9, 1), "score": r.score}
+        out[name] = row
+    return out
+
+
+def bench_serving(sw, ctx, rates=(10.0, 100.0, 1000.0), count: int = 40):
     """Poisson arrivals of pairs with L log-uniform in [1e3, 1e6] (70 % score-only,
     30 % alignment), submitted at their arrival times to a 4-worker server."""
     import threading
@@ -316,11 +365,8 @@ def main():
         launches += r.stats["kernel_launches"]
     torch.cuda.synchronize()
     clk = clocks.stop()
-    total = sum(times)
+    total = _max_over_ranks(dist, sum(times), "cuda")
     if dist:
-        t = torch.tensor([total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
         dist.barrier()
 
     # end to end through the public API: host buffers in, CIGAR back on the host
@@ -332,11 +378,7 @@ def main():
         re = step(dev=False)
         e2e_times.append(time.perf_counter() - t0)
     assert (re.score, re.cigar) == (r.score, r.cigar)
-    e2e_total = sum(e2e_times)
-    if dist:
-        t = torch.tensor([e2e_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = _max_over_ranks(dist, sum(e2e_times), "cuda")
 
     extras = {}
     if not args.no_extras and rank == 0:
@@ -348,7 +390,10 @@ def main():
             "gcups_pruned": round(n * m / rs.stats["ms_forward"] / 1e6, 1),
             "gcups_unpruned": round(n * m / rn.stats["ms_forward"] / 1e6, 1),
             "ms_pruned": round(rs.stats["ms_forward"], 1), "ms_unpruned": round(rn.stats["ms_forward"], 1),
-            "tiles_pruned_frac": round(rs.stats["tiles_pruned"] / max(1, rs.stats["tiles_total"]), 4)}
+            "tiles_pruned_frac": round(rs.stats["tiles_pruned"] / max(1, rs.stats["tiles_total"]), 4),
+            "roofline_frac_unpruned": round(rn.stats["fwd_cells"] * OPS_PER_CELL / (rn.stats["ms_forward"] / 1e3) /
+                                            (torch.cuda.get_device_properties(local).multi_processor_count *
+                                             INT_LANES_PER_CLK * (clk["sm_mhz"] or 2070) * 1e6), 4)}
         # the plain GPU path (one thread per cell, one launch per anti-diagonal)
         ps = 20_000
         rp = sw.sw_score_plain(ctx, a[:ps], b[:ps])
@@ -360,13 +405,14 @@ def main():
                                                             (ps * ps / rp.stats["ms_forward"] / 1e6), 1)}
 
     if not args.no_extras and rank == 0:
+        extras["small_pairs"] = bench_small_pairs(sw, ctx)
         extras["batch"] = bench_batch(sw, ctx)
         extras["serving"] = bench_serving(sw, ctx)
 
     if rank != 0:
         return
-    value = ws * n * m * args.steps / total / 1e9
-    e2e = ws * n * m * args.steps / e2e_total / 1e9
+    value = _job_gcups(ws, n * m, args.steps, total)
+    e2e = _job_gcups(ws, n * m, args.steps, e2e_total)
     fwd_s = statistics.mean(fwd_ms) / 1e3
     f_clk = (clk["sm_mhz"] or 2070) * 1e6
     import ctypes
@@ -377,14 +423,9 @@ def main():
         "metric": "GCUPS", "value": round(value, 2), "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int16", "data": "synthetic",
-        "config": {"workload": f"pair_5m: {n} x {m} DNA pair (GC 41%, tandem repeats, 10% subst, 1% ins, "
-                               f"1% del, 20 kbp inversion, 50 kbp deletion); sw_align = score + end, "
-                               f"start, CIGAR; match +1, mismatch -3, gap 5 + 2(k-1)",
-                   "l2": "flushed before every step (256 MiB write); step working set < L2",
-                   "arithmetic": "exact integer scores: forward and start passes on int16x2 DPX lanes with "
-                                 "per-warp offsets, int32 boundary rows and reconstruction",
-                   "score": r.score, "a": [r.a_begin, r.a_end], "b": [r.b_begin, r.b_end],
-                   "cigar_len": len(r.cigar or ""), "parallelism": f"replicas x{ws}"},
+        "config": _config(n, m, ws),
+        "result": {"score": r.score, "a": [r.a_begin, r.a_end], "b": [r.b_begin, r.b_end],
+                   "cigar_len": len(r.cigar or "")},
         "phases_ms": {"forward": round(r.stats["ms_forward"], 1), "start": round(r.stats["ms_start"], 1),
                       "reconstruct": round(r.stats["ms_align"], 1), "levels": r.stats["levels"]},
         "roofline": {"bound": "alu", "kernel": "fwd16_kernel (forward score pass, int16x2 offset lanes, pruned)",

@@ -69,6 +69,9 @@ typedef enum {
 #define SW_FLAG_FORCE_INT16   0x10  /* batch: int16x2 lanes even when the static bound
                                        does not rule out overflow (overflow is detected
                                        and the pair re-run in int32) */
+#define SW_FLAG_BOTH_STRANDS  0x20  /* batch: align every pair against B and against its
+                                       reverse complement in the same batch; keep the
+                                       strand with the higher score (forward on a tie) */
 
 /* Substitution scores and gap costs.  Codes are 0..alphabet-1 (DNA: A0 C1 G2 T3,
  * N4).  matrix == NULL uses match on identical codes below 4 and mismatch
@@ -105,6 +108,10 @@ typedef struct {
     char *cigar;                              /* library-owned; free with sw_result_free */
     int64_t cigar_len;
     sw_stats stats;
+    int32_t strand;       /* 0: B as given; 1 (SW_FLAG_BOTH_STRANDS only): the reverse
+                             complement of B scored higher, and b_begin, b_end and the
+                             CIGAR refer to revcomp(B) */
+    int32_t reserved;
 } sw_result;
 
 typedef struct {
@@ -179,7 +186,14 @@ int sw_align(sw_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64_t
  * pairs' row bands).  outs[count] receives one result per pair, in input order.
  * With SW_FLAG_SCORE_ONLY only score and end point are produced; otherwise each
  * pair is also aligned.  Pairs whose score bound fits int16 run on int16x2
- * lanes unless SW_FLAG_FORCE_INT32. */
+ * lanes unless SW_FLAG_FORCE_INT32.
+ *
+ * SW_FLAG_BOTH_STRANDS (Sec. 3 runs each pair against both strands of B; DNA
+ * codes, alphabet 4 or 5): the batch holds every pair twice, with B and with
+ * revcomp(B) (A0 C1 G2 T3 complement as c <-> 3 - c, N stays), and outs[p] is
+ * the strand with the higher score, the forward one on a tie; outs[p].strand
+ * says which.  Each result's stats.cells counts both strands.  count may be
+ * at most 2^30 - 1 with this flag. */
 int sw_align_batch(sw_ctx *ctx, const sw_pair *pairs, int32_t count,
                    const sw_scheme *scheme, int32_t flags, sw_result *outs);
 

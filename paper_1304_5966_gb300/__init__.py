@@ -30,6 +30,7 @@ SW_FLAG_SCORE_ONLY = 0x2
 SW_FLAG_NO_PRUNE = 0x4
 SW_FLAG_FORCE_INT32 = 0x8
 SW_FLAG_FORCE_INT16 = 0x10
+SW_FLAG_BOTH_STRANDS = 0x20
 SW_OPT_ROWS_PER_THREAD, SW_OPT_WARPS_PER_SM, SW_OPT_TIMEOUT_MS, SW_OPT_FAULT_BAND, \
     SW_OPT_CKPT_BANDS, SW_OPT_LEAF_CELLS, SW_OPT_FORWARD_LANES, SW_OPT_TRACE, SW_OPT_AUTOTUNE = range(1, 10)
 
@@ -60,16 +61,17 @@ class _Stats(ctypes.Structure):
 class _Result(ctypes.Structure):
     _fields_ = [("score", ctypes.c_int64), ("a_begin", ctypes.c_int64), ("a_end", ctypes.c_int64),
                 ("b_begin", ctypes.c_int64), ("b_end", ctypes.c_int64),
-                ("cigar", ctypes.c_void_p), ("cigar_len", ctypes.c_int64), ("stats", _Stats)]
+                ("cigar", ctypes.c_void_p), ("cigar_len", ctypes.c_int64), ("stats", _Stats),
+                ("strand", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 # numpy view of a _Result array (same layout): score, coordinates, the CIGAR
 # pointer and the per-pair cell count, read in bulk for large batches
-_RESULT_DTYPE = np.dtype({"names": ["score", "a_begin", "a_end", "b_begin", "b_end", "cigar", "cells"],
-                          "formats": ["<i8"] * 5 + ["<u8", "<i8"],
+_RESULT_DTYPE = np.dtype({"names": ["score", "a_begin", "a_end", "b_begin", "b_end", "cigar", "cells", "strand"],
+                          "formats": ["<i8"] * 5 + ["<u8", "<i8", "<i4"],
                           "offsets": [_Result.score.offset, _Result.a_begin.offset, _Result.a_end.offset,
                                       _Result.b_begin.offset, _Result.b_end.offset, _Result.cigar.offset,
-                                      _Result.stats.offset + _Stats.cells.offset],
+                                      _Result.stats.offset + _Stats.cells.offset, _Result.strand.offset],
                           "itemsize": ctypes.sizeof(_Result)})
 
 
@@ -147,6 +149,7 @@ class Result:
     b_end: int
     cigar: str | None
     stats: dict = field(default_factory=dict)
+    strand: int = 0          # 1: the reverse complement of B (SW_FLAG_BOTH_STRANDS)
 
 
 class Context:
@@ -218,7 +221,8 @@ def _result(r: _Result) -> Result:
     if r.cigar:
         cig = ctypes.string_at(r.cigar, r.cigar_len).decode()
     st = {f: getattr(r.stats, f) for f, _ in _Stats._fields_}
-    return Result(int(r.score), int(r.a_begin), int(r.a_end), int(r.b_begin), int(r.b_end), cig, st)
+    return Result(int(r.score), int(r.a_begin), int(r.a_end), int(r.b_begin), int(r.b_end), cig, st,
+                  int(r.strand))
 
 
 def _pairwise(fn, ctx, a, b, scheme, flags):
@@ -266,7 +270,9 @@ def _host_pairs(pairs):
 
 
 def sw_align_batch(ctx: Context, pairs, scheme: Scheme | None = None, flags: int = 0):
-    """Many pairs in one persistent launch; returns one Result per pair, in order."""
+    """Many pairs in one persistent launch; returns one Result per pair, in order.
+    With SW_FLAG_BOTH_STRANDS each pair is also run against the reverse
+    complement of B and the better strand kept (Result.strand)."""
     keep = []
     dev = None
     packed = _host_pairs(pairs) if len(pairs) else None
@@ -301,6 +307,7 @@ def _batch_results(outs, count: int):
                          dtype=_RESULT_DTYPE, count=count)
     score, a0, a1 = view["score"].tolist(), view["a_begin"].tolist(), view["a_end"].tolist()
     b0, b1, cells = view["b_begin"].tolist(), view["b_end"].tolist(), view["cells"].tolist()
+    strand = view["strand"].tolist()
     has_cigar = view["cigar"].any()
     res = []
     for k in range(count):
@@ -309,7 +316,7 @@ def _batch_results(outs, count: int):
             cig = ctypes.string_at(outs[k].cigar, outs[k].cigar_len).decode()
             lib().sw_result_free(ctypes.byref(outs[k]))
         st = {f: getattr(outs[0].stats, f) for f, _ in _Stats._fields_} if k == 0 else {"cells": cells[k]}
-        res.append(Result(score[k], a0[k], a1[k], b0[k], b1[k], cig, st))
+        res.append(Result(score[k], a0[k], a1[k], b0[k], b1[k], cig, st, strand[k]))
     return res
 
 

@@ -37,4 +37,10 @@ int run_forward16(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &j
 cudaError_t reverse_segments_launch(const uint8_t *src, uint8_t *dst, const int64_t *src_off,
                                     const int64_t *dst_off, const int32_t *len, int count, cudaStream_t s);
 
+// reverse complement of count segments (same offsets in src and dst), one block each
+cudaError_t revcomp_segments_launch(const uint8_t *src, uint8_t *dst, const int64_t *off, const int32_t *len,
+                                    int count, cudaStream_t s);
+// DNA complement of one code (A0 C1 G2 T3: c <-> 3 - c); N (4) and other codes stay
+inline uint8_t complement_code(uint8_t c) { return c < 4 ? (uint8_t)(3 - c) : c; }
+
 }  // namespace swgb

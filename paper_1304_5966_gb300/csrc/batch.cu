@@ -129,7 +129,8 @@ int batch_forward(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const uin
 
 }  // namespace swgb
 
-extern "C" int sw_align_batch(sw_ctx *ctx, const sw_pair *pairs, int32_t count, const sw_scheme *scheme,
+// One strand: every pair as given.
+static int align_batch_strand(sw_ctx *ctx, const sw_pair *pairs, int32_t count, const sw_scheme *scheme,
                               int32_t flags, sw_result *outs)
 {
     if (!ctx || !outs || count < 0 || (count > 0 && !pairs)) return SW_EINVAL;
@@ -272,4 +273,100 @@ extern "C" int sw_align_batch(sw_ctx *ctx, const sw_pair *pairs, int32_t count, 
     }
     outs[0].stats.kernel_launches = ctx->launches - l0;
     return SW_OK;
+}
+
+// Both strands (Sec. 3 runs each chromosome pair against B and its reverse
+// complement): the batch holds every pair twice, once with B and once with
+// revcomp(B), and each pair keeps the strand with the higher score (the
+// forward strand on a tie).  The reverse complements are made on the host for
+// host inputs and by one kernel over all pairs for device inputs.
+static int align_batch_both(sw_ctx *ctx, const sw_pair *pairs, int32_t count, const sw_scheme *scheme,
+                            int32_t flags, sw_result *outs)
+{
+    SchemeDev sc;
+    int st = build_scheme(scheme, &sc);
+    if (st) { ctx->last_error = "invalid scheme"; return st; }
+    if (sc.alphabet > 5) { ctx->last_error = "both strands need DNA codes (alphabet 4 or 5)"; return SW_EINVAL; }
+    if (count > INT32_MAX / 2) return SW_EINVAL;
+    const bool dev = (flags & SW_FLAG_DEVICE_INPUT) != 0;
+    std::vector<int64_t> off(count);
+    int64_t tb = 0;
+    for (int p = 0; p < count; ++p) {
+        if (pairs[p].m < 0 || pairs[p].n < 0 || (pairs[p].m && !pairs[p].b)) return SW_EINVAL;
+        if (pairs[p].m > INT32_MAX) return SW_EINVAL;
+        off[p] = tb;
+        tb += pairs[p].m;
+    }
+    std::vector<sw_pair> ext(2 * (size_t)count);
+    std::vector<uint8_t> hrc;
+    Scope s(ctx->arena);
+    const uint8_t *rc = nullptr;
+    if (!dev) {
+        hrc.resize((size_t)tb + 1);
+        for (int p = 0; p < count; ++p) {
+            const uint8_t *b = pairs[p].b;
+            uint8_t *d = hrc.data() + off[p];
+            const int64_t m = pairs[p].m;
+            for (int64_t i = 0; i < m; ++i) d[i] = complement_code(b[m - 1 - i]);
+        }
+        rc = hrc.data();
+    } else {
+        uint8_t *dg = s.get<uint8_t>((size_t)tb + 16), *drc = s.get<uint8_t>((size_t)tb + 16);
+        int64_t *doff = s.get<int64_t>((size_t)count);
+        int32_t *dlen = s.get<int32_t>((size_t)count);
+        if (s.failed()) { ctx->last_error = "workspace too small for the reverse complements"; return SW_ENOMEM; }
+        std::vector<int32_t> len(count);
+        cudaError_t e;
+        cudaSetDevice(ctx->device);
+        for (int p = 0; p < count; ++p) {
+            len[p] = (int32_t)pairs[p].m;
+            if (len[p] && (e = cudaMemcpyAsync(dg + off[p], pairs[p].b, (size_t)len[p], cudaMemcpyDeviceToDevice,
+                                               ctx->stream)))
+                return set_cuda_error(ctx, e, "both strands gather");
+        }
+        if ((e = cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice, ctx->stream)) ||
+            (e = cudaMemcpyAsync(dlen, len.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, ctx->stream)) ||
+            (e = revcomp_segments_launch(dg, drc, doff, dlen, count, ctx->stream)))
+            return set_cuda_error(ctx, e, "both strands reverse complement");
+        ctx->launches += 1;
+        rc = drc;
+    }
+    for (int p = 0; p < count; ++p) {
+        ext[p] = pairs[p];
+        ext[(size_t)count + p] = sw_pair{pairs[p].a, pairs[p].n, rc + off[p], pairs[p].m};
+    }
+    std::vector<sw_result> tmp(2 * (size_t)count);
+    st = align_batch_strand(ctx, ext.data(), 2 * count, scheme, flags & ~SW_FLAG_BOTH_STRANDS, tmp.data());
+    if (st) {
+        for (sw_result &r : tmp) sw_result_free(&r);
+        return st;
+    }
+    const sw_stats call_stats = tmp[0].stats;
+    for (int p = 0; p < count; ++p) {
+        sw_result &f = tmp[p], &r = tmp[(size_t)count + p];
+        const bool rev = r.score > f.score;
+        sw_result &win = rev ? r : f, &lose = rev ? f : r;
+        outs[p] = win;                  // takes over the winner's CIGAR
+        win.cigar = nullptr;
+        sw_result_free(&lose);
+        outs[p].strand = rev ? 1 : 0;
+        outs[p].stats = sw_stats{};
+        outs[p].stats.cells = 2 * pairs[p].n * pairs[p].m;
+    }
+    outs[0].stats = call_stats;
+    outs[0].stats.cells = 2 * pairs[0].n * pairs[0].m;
+    return SW_OK;
+}
+
+extern "C" int sw_align_batch(sw_ctx *ctx, const sw_pair *pairs, int32_t count, const sw_scheme *scheme,
+                              int32_t flags, sw_result *outs)
+{
+    if (!(flags & SW_FLAG_BOTH_STRANDS)) return align_batch_strand(ctx, pairs, count, scheme, flags, outs);
+    if (!ctx || !outs || count < 0 || (count > 0 && !pairs)) return SW_EINVAL;
+    for (int p = 0; p < count; ++p) {
+        std::memset(&outs[p], 0, sizeof(sw_result));
+        outs[p].a_begin = outs[p].a_end = outs[p].b_begin = outs[p].b_end = -1;
+    }
+    if (count == 0) return SW_OK;
+    return align_batch_both(ctx, pairs, count, scheme, flags, outs);
 }

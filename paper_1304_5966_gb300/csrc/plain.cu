@@ -99,6 +99,26 @@ cudaError_t reverse_segments_launch(const uint8_t *src, uint8_t *dst, const int6
     return cudaGetLastError();
 }
 
+// one block per segment: dst[off + i] = complement(src[off + len - 1 - i])
+// (DNA codes A0 C1 G2 T3 pair as c <-> 3 - c; N and any other code stay)
+__global__ void revcomp_segments_kernel(const uint8_t *src, uint8_t *dst, const int64_t *off, const int32_t *len)
+{
+    const int k = blockIdx.x;
+    const int64_t o = off[k];
+    const int L = len[k];
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const uint8_t c = src[o + L - 1 - i];
+        dst[o + i] = c < 4 ? (uint8_t)(3 - c) : c;
+    }
+}
+cudaError_t revcomp_segments_launch(const uint8_t *src, uint8_t *dst, const int64_t *off, const int32_t *len,
+                                    int count, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    revcomp_segments_kernel<<<count, 256, 0, s>>>(src, dst, off, len);
+    return cudaGetLastError();
+}
+
 __global__ void fill_i32_kernel(int32_t *p, int32_t v, int64_t count)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;

@@ -45,3 +45,27 @@ def test_null_arguments_are_rejected(lib):
     assert lib.sw_align(None, None, 0, None, 0, None, 0, None) == 1
     assert lib.sw_align_batch(None, None, 0, None, 0, None) == 1
     assert lib.sw_ctx_set_option(None, 1, 16) == 1
+
+
+def test_struct_layout_matches_header(tmp_path):
+    """The binding's ctypes mirrors of the header's structs have the C
+    compiler's sizes and field offsets (a field added to one side only would
+    shift every later field and every result of a batch)."""
+    import subprocess
+    import paper_1304_5966_gb300 as sw
+    structs = {"sw_scheme": sw._Scheme, "sw_stats": sw._Stats, "sw_result": sw._Result, "sw_pair": sw._Pair}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "swgb.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.rsplit(" ", 1) for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for cname, py in structs.items():
+        assert int(got[f"{cname} size"]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[f"{cname} {f}"]) == getattr(py, f).offset, (cname, f)

@@ -154,6 +154,60 @@ def test_batch_4096_golden(sw, ctx):
     assert [_se(r) for r in got] == want
 
 
+def _strand_pairs(seed):
+    """Pairs whose best strand is B as given, its reverse complement, or
+    either (a B that is its own reverse complement: a tie)."""
+    st = synth.Rng(seed).stream()
+    pairs = []
+    for t in range(36):
+        n = int(synth.log_uniform_int(st, 20, 2500, 1)[0])
+        a, b = synth.related_pair(n, seed=seed * 100 + t)
+        if t % 3 == 1:
+            b = synth.revcomp(b)
+        elif t % 3 == 2:
+            a, b = synth.random_pair(n, int(synth.log_uniform_int(st, 1, 2500, 1)[0]), seed=seed * 100 + t)
+        pairs.append((a, b))
+    x = synth.random_bases(st, 300)
+    pairs.append((synth.random_bases(st, 900), np.concatenate([x, synth.revcomp(x)])))   # tie
+    pairs.append((x.copy(), np.concatenate([x, synth.revcomp(x)])))                      # tie, high score
+    pairs.append((x.copy(), np.zeros(0, np.uint8)))                                      # empty B
+    return pairs
+
+
+def _best_strand(a, b, score_only):
+    """The oracle on both strands; the reverse one only when strictly better."""
+    rb = synth.revcomp(b)
+    if score_only:
+        f, r = oracle.local_score(a, b), oracle.local_score(a, rb)
+        w, strand = (r, 1) if r[0] > f[0] else (f, 0)
+        return (w if w[0] else (0, -1, -1)), strand
+    f, r = oracle.align(a, b), oracle.align(a, rb)
+    w, strand = (r, 1) if r.score > f.score else (f, 0)
+    return (w.score, w.a_begin, w.a_end, w.b_begin, w.b_end, w.cigar), strand
+
+
+def test_both_strands(sw, ctx):
+    """SW_FLAG_BOTH_STRANDS: each pair runs against B and revcomp(B) in one batch
+    and keeps the strand with the higher score (forward on a tie), score-only and
+    aligned, host and device inputs."""
+    import torch
+    pairs = _strand_pairs(5)
+    so = sw.sw_align_batch(ctx, pairs, flags=sw.SW_FLAG_SCORE_ONLY | sw.SW_FLAG_BOTH_STRANDS)
+    al = sw.sw_align_batch(ctx, pairs, flags=sw.SW_FLAG_BOTH_STRANDS)
+    dev = [(torch.from_numpy(a.copy()).cuda(), torch.from_numpy(b.copy()).cuda()) for a, b in pairs]
+    ad = sw.sw_align_batch(ctx, dev, flags=sw.SW_FLAG_BOTH_STRANDS)
+    strands = []
+    for k, (a, b) in enumerate(pairs):
+        want, strand = _best_strand(a, b, True)
+        assert (_se(so[k]), so[k].strand) == (want, strand), k
+        want, strand = _best_strand(a, b, False)
+        for r in (al[k], ad[k]):
+            assert ((r.score, r.a_begin, r.a_end, r.b_begin, r.b_end, r.cigar or ""), r.strand) == (want, strand), k
+        strands.append(strand)
+    assert 0 < sum(strands) < len(strands)
+    assert al[-2].strand == 0 and al[-2].score > 0 and al[-3].strand == 0
+
+
 def test_band_height_tuning(sw):
     """The first batch of a shape times each int16x2 band height and keeps the
     fastest for that shape; tuned, cached and untuned calls return the same
