@@ -39,6 +39,10 @@ sys.path.insert(0, ROOT)
 OPS_PER_CELL = 3.5        # minimal cell update on int16x2 DPX lanes: 7 ops per two cells
 INT_LANES_PER_CLK = 64    # measured: DPX (32- and 16x2-bit) / PRMT lane ops per clock per SM
 SAMPLE_EDGE = 40_000      # CPU oracle sample: the first 40k x 40k of the pair
+# DRAM bytes (read + write) of one forward launch of this step, from one ncu
+# capture of the timed step's forward pass (profiles/fwd16_kernel_dram_pair_5m_bench.md);
+# set to None whenever the forward kernel changes
+FWD_TRAFFIC_BYTES = 329_223_936 + 3_348_415_488
 
 
 def _args():
@@ -430,7 +434,8 @@ def main():
                       "reconstruct": round(r.stats["ms_align"], 1), "levels": r.stats["levels"]},
         "roofline": {"bound": "alu", "kernel": "fwd16_kernel (forward score pass, int16x2 offset lanes, pruned)",
                      "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "frac": round(achieved / peak, 4), "traffic": FWD_TRAFFIC_BYTES,
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "cells_per_launch": int(statistics.mean(fwd_cells)), "ops_per_cell": OPS_PER_CELL,
                      "peak_basis": f"{sms} SMs x {INT_LANES_PER_CLK} int lane-ops/clk x {f_clk / 1e6:.0f} MHz (sampled)"},
         "e2e": {"value": round(e2e, 2), "unit": "GCUPS", "h2d_bytes_per_step": n + m,
