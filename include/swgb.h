@@ -168,6 +168,20 @@ enum {
 };
 int sw_ctx_set_option(sw_ctx *ctx, int option, int64_t value);
 
+/* The SW_OPT_AUTOTUNE table (batch shape -> int16x2 band height) as text, so a
+ * later process on the same GPU model can skip the timing runs (the paper has no
+ * autotuner; this is a deployment aid).  The text is a header line naming the
+ * format and the device model, then one "<shape key, hex> <rows per lane>" line
+ * per batch shape.
+ * sw_ctx_tuning_export: writes the text and its NUL into buf[0..cap) and the
+ * text's length into *len; SW_ENOMEM (with *len set) when cap is too small.
+ * sw_ctx_tuning_import: merges such a text into the context's table; SW_EINVAL,
+ * leaving the table unchanged, when the text is malformed, names a band height
+ * the library does not have, or was written on another GPU model.  Either call
+ * takes the context's call lock; neither touches the GPU. */
+int sw_ctx_tuning_export(sw_ctx *ctx, char *buf, uint64_t cap, uint64_t *len);
+int sw_ctx_tuning_import(sw_ctx *ctx, const char *text);
+
 /* Score and end point (Sec. 2, wavefront and pruning paragraphs).  a[0..n),
  * b[0..m) are codes below scheme->alphabet, host memory unless
  * SW_FLAG_DEVICE_INPUT.  Fills score, a_end, b_end; a_begin = b_begin = -1;

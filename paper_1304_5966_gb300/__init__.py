@@ -99,6 +99,8 @@ def lib():
         L.sw_strerror.argtypes = [ctypes.c_int]
         L.sw_strerror.restype = ctypes.c_char_p
         L.sw_ctx_set_option.argtypes = [P, ctypes.c_int, i64]
+        L.sw_ctx_tuning_export.argtypes = [P, ctypes.c_char_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
+        L.sw_ctx_tuning_import.argtypes = [P, ctypes.c_char_p]
         for fn in ("sw_score", "sw_align", "sw_score_plain"):
             getattr(L, fn).argtypes = [P, P, i64, P, i64, ctypes.POINTER(_Scheme), i32,
                                        ctypes.POINTER(_Result)]
@@ -173,6 +175,20 @@ class Context:
 
     def set_option(self, option: int, value: int):
         _check(self, lib().sw_ctx_set_option(self.handle, option, int(value)))
+
+    def tuning_export(self) -> str:
+        """The batch autotuner's table (batch shape -> band height) as text."""
+        n = ctypes.c_uint64()
+        st = lib().sw_ctx_tuning_export(self.handle, None, 0, ctypes.byref(n))
+        if st not in (SW_OK, SW_ENOMEM):
+            _check(self, st)
+        buf = ctypes.create_string_buffer(n.value + 1)
+        _check(self, lib().sw_ctx_tuning_export(self.handle, buf, n.value + 1, ctypes.byref(n)))
+        return buf.value.decode()
+
+    def tuning_import(self, text: str):
+        """Merge a table written by tuning_export on the same GPU model."""
+        _check(self, lib().sw_ctx_tuning_import(self.handle, text.encode()))
 
     def close(self):
         if getattr(self, "handle", None):

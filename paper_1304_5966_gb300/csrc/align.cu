@@ -47,6 +47,7 @@ static int run_label_level(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, 
                            sw_stats *stats, const std::vector<const RootGuide *> &guides)
 {
     const int np = (int)subs.size();
+    Range nv("swgb label pass");
     cross.assign(np, {});
     sinkv.assign(np, 0);
     if (np == 0) return SW_OK;
@@ -252,6 +253,7 @@ static int run_leaves(sw_ctx *ctx, const SchemeDev &sc, const uint8_t *dA, const
                       const std::vector<Sub> &subs, int max_cells, std::vector<std::string> &ops)
 {
     const int np = (int)subs.size();
+    Range nv("swgb leaves");
     ops.assign(np, std::string());
     if (np == 0) return SW_OK;
     Scope s(ctx->arena);
@@ -540,6 +542,7 @@ extern "C" int sw_align(sw_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t 
     std::memset(out, 0, sizeof *out);
     out->a_begin = out->a_end = out->b_begin = out->b_end = -1;
     std::lock_guard<std::mutex> g(ctx->call_mu);
+    Range nv("swgb sw_align");
     SchemeDev sc;
     int st = build_scheme(scheme, &sc);
     if (st) { ctx->last_error = "invalid scheme"; return st; }

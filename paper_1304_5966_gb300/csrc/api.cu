@@ -126,6 +126,7 @@ static int run_forward_impl(sw_ctx *ctx, const SchemeDev &sc, const std::vector<
                             sw_stats *stats, float *ms)
 {
     const int np = (int)jobs.size();
+    Range nv(np && jobs[0].mode == FWD_ANCHORED ? "swgb start-point pass" : "swgb forward pass");
     res.assign(np, make_int4(0, 0, 0, 0));
     if (ovf) ovf->assign(np, 0);
     if (np == 0) return SW_OK;
@@ -413,6 +414,7 @@ int sw_ctx_create(int device, void *stream, void *workspace, uint64_t workspace_
     cudaDeviceProp prop;
     if ((e = cudaGetDeviceProperties(&prop, device))) { delete c; return set_cuda_error(nullptr, e, "props"); }
     c->sms = prop.multiProcessorCount;
+    c->gpu_name = prop.name;
     if (workspace) {
         c->ws = (char *)workspace;
     } else {
@@ -486,6 +488,7 @@ int sw_score(sw_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64_t
     if (!ctx || !out) return SW_EINVAL;
     clear_result(out);
     std::lock_guard<std::mutex> g(ctx->call_mu);
+    Range nv("swgb sw_score");
     SchemeDev sc;
     int st = build_scheme(scheme, &sc);
     if (st) { ctx->last_error = "invalid scheme"; return st; }

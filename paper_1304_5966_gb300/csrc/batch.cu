@@ -11,6 +11,7 @@
 // requests then run their start-point passes as one batched anchored launch and
 // their reconstructions as one recursion over all pairs.
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -140,6 +141,7 @@ static int align_batch_strand(sw_ctx *ctx, const sw_pair *pairs, int32_t count, 
     }
     if (count == 0) return SW_OK;
     std::lock_guard<std::mutex> g(ctx->call_mu);
+    Range nv("swgb sw_align_batch");
     SchemeDev sc;
     int st = build_scheme(scheme, &sc);
     if (st) { ctx->last_error = "invalid scheme"; return st; }
@@ -369,4 +371,56 @@ extern "C" int sw_align_batch(sw_ctx *ctx, const sw_pair *pairs, int32_t count, 
     }
     if (count == 0) return SW_OK;
     return align_batch_both(ctx, pairs, count, scheme, flags, outs);
+}
+
+// The autotuner's table as text: a header line with the device model, then one
+// "shape-key band-height" line per batch shape (keys as written by
+// batch_shape_key, in hexadecimal).
+static const char *kTuneHeader = "swgb-tuning 1 ";
+
+extern "C" int sw_ctx_tuning_export(sw_ctx *ctx, char *buf, uint64_t cap, uint64_t *len)
+{
+    if (!ctx || !len || (cap && !buf)) return SW_EINVAL;
+    std::lock_guard<std::mutex> g(ctx->call_mu);
+    std::string out = std::string(kTuneHeader) + ctx->gpu_name + "\n";
+    char line[64];
+    for (const auto &kv : ctx->tuned_rpt16) {
+        snprintf(line, sizeof line, "%llx %d\n", (unsigned long long)kv.first, kv.second);
+        out += line;
+    }
+    *len = out.size();
+    if (out.size() + 1 > cap) return SW_ENOMEM;
+    std::memcpy(buf, out.c_str(), out.size() + 1);
+    return SW_OK;
+}
+
+extern "C" int sw_ctx_tuning_import(sw_ctx *ctx, const char *text)
+{
+    if (!ctx || !text) return SW_EINVAL;
+    std::lock_guard<std::mutex> g(ctx->call_mu);
+    const std::string t(text);
+    const std::string head = std::string(kTuneHeader) + ctx->gpu_name + "\n";
+    if (t.compare(0, head.size(), head) != 0) {
+        ctx->last_error = "tuning table from another format or GPU model";
+        return SW_EINVAL;
+    }
+    std::map<uint64_t, int> add;
+    size_t pos = head.size();
+    while (pos < t.size()) {
+        size_t eol = t.find('\n', pos);
+        if (eol == std::string::npos) eol = t.size();
+        const std::string ln = t.substr(pos, eol - pos);
+        pos = eol + 1;
+        if (ln.empty()) continue;
+        unsigned long long key = 0;
+        int rpt = 0;
+        char extra = 0;
+        if (sscanf(ln.c_str(), "%llx %d %c", &key, &rpt, &extra) != 2 || !fwd16_rpt_supported(rpt)) {
+            ctx->last_error = "malformed tuning line: " + ln;
+            return SW_EINVAL;
+        }
+        add[(uint64_t)key] = rpt;
+    }
+    for (const auto &kv : add) ctx->tuned_rpt16[kv.first] = kv.second;
+    return SW_OK;
 }

@@ -7,11 +7,23 @@
 #include <string>
 #include <vector>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/swgb.h"
 #include "kernels.h"
 
 namespace swgb {
+
+// NVTX range over the current scope, named after a library phase: shows the
+// phases on the host timeline of Nsight Systems and filters Nsight Compute
+// (--nvtx --nvtx-include).  NVTX v3 is header-only and does nothing unless a
+// tool is attached.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 // First-fit sub-allocator over the context's device workspace (256-byte aligned).
 class Arena {
@@ -129,6 +141,7 @@ struct sw_ctx {
     std::mutex call_mu;
     int64_t launches = 0;          // kernels launched by this context (all calls)
     std::map<uint64_t, int> tuned_rpt16;   // batch shape -> fastest int16x2 band height
+    std::string gpu_name;                  // device model the tuned table was measured on
 };
 
 namespace swgb {

@@ -231,3 +231,33 @@ def test_band_height_tuning(sw):
             assert got[0] == got[1] == got[2] == want[k], k
     finally:
         c.close()
+
+
+def test_tuning_table_export_import(sw):
+    """The autotuner's table moves between contexts as text: a context that
+    imports it runs the batch shape at the stored band height without timing
+    it, with the same results; a table naming another GPU model or holding a
+    malformed line is refused and changes nothing."""
+    c1 = sw.sw_ctx_create(0, workspace_bytes=1 << 30)
+    c2 = sw.sw_ctx_create(0, workspace_bytes=1 << 30)
+    try:
+        pairs = _mixed_pairs(64, seed=72, lo=200, hi=2500)
+        first = sw.sw_align_batch(c1, pairs, flags=sw.SW_FLAG_SCORE_ONLY)
+        assert first[0].stats["tuned"] == 1
+        text = c1.tuning_export()
+        lines = text.splitlines()
+        assert lines[0].startswith("swgb-tuning 1 ") and len(lines) == 2
+        for bad in (text.replace("swgb-tuning 1 ", "swgb-tuning 1 other "),
+                    lines[0] + "\nzz 16\n", lines[0] + "\n1f 12\n"):
+            with pytest.raises(sw.SwError):
+                c2.tuning_import(bad)
+        assert c2.tuning_export() == lines[0] + "\n"
+        c2.tuning_import(text)
+        assert c2.tuning_export() == text
+        again = sw.sw_align_batch(c2, pairs, flags=sw.SW_FLAG_SCORE_ONLY)
+        assert again[0].stats["tuned"] == 0
+        assert again[0].stats["band_rows"] == first[0].stats["band_rows"]
+        assert [_se(r) for r in again] == [_se(r) for r in first]
+    finally:
+        c1.close()
+        c2.close()
