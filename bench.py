@@ -246,6 +246,31 @@ def bench_batch(sw, ctx, reps: int = 3):
                     "single-pair path timed on every 16th pair, plain path on every 256th"}
 
 
+def bench_checkpointed(sw, ctx, ta, tb, one_pass):
+    """The pruned score pass as a checkpointed job: segments of one wave of
+    bands, a host snapshot after each; same score and end point as one pass."""
+    try:
+        t0 = time.perf_counter()
+        job = sw.sw_score_job_create(ctx, ta, tb)
+        snap_bytes, segs = 0, 0
+        while True:
+            jdone, jtotal = job.run(job.wave_bands)
+            snap_bytes = len(job.snapshot())
+            segs += 1
+            if jdone == jtotal:
+                break
+        rj = job.result()
+        job.close()
+        job_s = time.perf_counter() - t0
+    except Exception as e:          # a side measurement never takes the bench line down
+        return {"error": str(e)}
+    return {"segments": segs, "bands": jtotal, "wave_bands": job.wave_bands,
+            "snapshot_mb": round(snap_bytes / 2 ** 20, 1), "wall_s": round(job_s, 2),
+            "kernel_ms": round(rj.stats["ms_forward"], 1),
+            "vs_one_pass_kernel": round(rj.stats["ms_forward"] / one_pass.stats["ms_forward"], 3),
+            "same_score_and_end": (rj.score, rj.a_end, rj.b_end) == (one_pass.score, one_pass.a_end, one_pass.b_end)}
+
+
 def bench_small_pairs(sw, ctx, reps: int = 9):
     """The 1 kbp pair (BASELINE config 1) and the 100 kbp pair (config 2):
     median wall latency of sw_align and of sw_score per call (host inputs,
@@ -398,6 +423,7 @@ def main():
             "roofline_frac_unpruned": round(rn.stats["fwd_cells"] * OPS_PER_CELL / (rn.stats["ms_forward"] / 1e3) /
                                             (torch.cuda.get_device_properties(local).multi_processor_count *
                                              INT_LANES_PER_CLK * (clk["sm_mhz"] or 2070) * 1e6), 4)}
+        extras["checkpointed_score_pass"] = bench_checkpointed(sw, ctx, ta, tb, rs)
         # the plain GPU path (one thread per cell, one launch per anti-diagonal)
         ps = 20_000
         rp = sw.sw_score_plain(ctx, a[:ps], b[:ps])

@@ -211,6 +211,51 @@ int sw_align(sw_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64_t
 int sw_align_batch(sw_ctx *ctx, const sw_pair *pairs, int32_t count,
                    const sw_scheme *scheme, int32_t flags, sw_result *outs);
 
+/* ---- Checkpointable score pass ------------------------------------------------
+ * The paper has no checkpoints; these calls let a chromosome-scale score pass
+ * stop and resume.  A job runs sw_score's forward pass (same lanes, band height,
+ * pruning and results) in segments of row bands.  Between segments its whole
+ * state is the boundary row (H and F of the last finished band's bottom row,
+ * the paper's O(n + 9m) memory; Sec. 2), the per-band results and the running
+ * best: sw_score_job_snapshot copies it to host memory, and
+ * sw_score_job_resume rebuilds a job from a snapshot, in this or another process
+ * on a GPU of the same model.  Each segment boundary drains and refills the band
+ * pipeline, so segments should be long (thousands of bands at 5 Mbp).
+ *
+ * sw_score_job_create: a, b and flags as for sw_score (SW_FLAG_DEVICE_INPUT,
+ *   SW_FLAG_NO_PRUNE); both sequences non-empty.  The job copies the sequences
+ *   and holds its device state in ctx's workspace until sw_score_job_destroy
+ *   (about 16 B per column of b plus 24 B per band).
+ * sw_score_job_run: runs up to `bands` more bands as one launch (bands < 0: all
+ *   that are left; 0: none, progress only) and reports the bands done, the total
+ *   and the wave: how many bands the GPU runs at once.  A launch ends when its
+ *   last band has crossed every column, with the GPU ever less busy meanwhile,
+ *   so segments that are whole waves add the least time (a segment shorter
+ *   than a wave leaves SMs idle throughout).  If the int16x2 lanes
+ *   overflow, the job restarts from band 0 on int32 lanes (bands_done drops to 0;
+ *   results are unchanged).
+ * sw_score_job_snapshot: writes the state into buf[0..cap) and its size into
+ *   *len; SW_ENOMEM (with *len set) when cap is too small.  Call with cap = 0 to
+ *   learn the size.  The snapshot is a header naming the inputs (sizes,
+ *   FNV-1a 64 fingerprints of both sequences, scheme, pruning, lanes, band
+ *   height) followed by raw device bytes.
+ * sw_score_job_resume: SW_EINVAL when the snapshot is malformed, of another
+ *   library version, or was taken for other sequences, scheme or pruning flag.
+ * sw_score_job_result: score, a_end, b_end and statistics once every band has
+ *   run; SW_EPENDING before.
+ * Every call takes the context's call lock; ctx must outlive the job. */
+typedef struct sw_score_job sw_score_job;
+int sw_score_job_create(sw_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64_t m,
+                        const sw_scheme *scheme, int32_t flags, sw_score_job **out);
+int sw_score_job_run(sw_score_job *job, int64_t bands, int64_t *bands_done, int64_t *bands_total,
+                     int64_t *wave_bands);
+int sw_score_job_snapshot(sw_score_job *job, void *buf, uint64_t cap, uint64_t *len);
+int sw_score_job_resume(sw_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64_t m,
+                        const sw_scheme *scheme, int32_t flags, const void *snapshot, uint64_t len,
+                        sw_score_job **out);
+int sw_score_job_result(sw_score_job *job, sw_result *out);
+void sw_score_job_destroy(sw_score_job *job);
+
 /* The plain GPU path used as the comparison baseline: one thread per cell of
  * each anti-diagonal, int32, no pruning, one launch per anti-diagonal.  Same
  * score and end point as sw_score. */

@@ -107,6 +107,14 @@ def lib():
         L.sw_align_batch.argtypes = [P, ctypes.POINTER(_Pair), i32, ctypes.POINTER(_Scheme), i32,
                                      ctypes.POINTER(_Result)]
         L.sw_score_static.argtypes = [P, i64, P, i64, ctypes.POINTER(_Scheme), P, ctypes.POINTER(_Result)]
+        L.sw_score_job_create.argtypes = [P, P, i64, P, i64, ctypes.POINTER(_Scheme), i32, ctypes.POINTER(P)]
+        L.sw_score_job_run.argtypes = [P, i64, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.sw_score_job_snapshot.argtypes = [P, P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
+        L.sw_score_job_resume.argtypes = [P, P, i64, P, i64, ctypes.POINTER(_Scheme), i32, P, ctypes.c_uint64,
+                                          ctypes.POINTER(P)]
+        L.sw_score_job_result.argtypes = [P, ctypes.POINTER(_Result)]
+        L.sw_score_job_destroy.argtypes = [P]
+        L.sw_score_job_destroy.restype = None
         L.sw_server_create.argtypes = [P, i32, ctypes.c_uint64, ctypes.POINTER(P)]
         L.sw_server_submit.argtypes = [P, P, i64, P, i64, ctypes.POINTER(_Scheme), i32,
                                        ctypes.POINTER(ctypes.c_uint64)]
@@ -352,6 +360,81 @@ def sw_score_static(a, b, scheme: Scheme | None = None, stream=None) -> Result:
     if st != SW_OK:
         raise SwError(st, f"sw_score_static: {lib().sw_strerror(st).decode()}")
     return _result(res)
+
+
+class ScoreJob:
+    """A score pass run in segments of row bands, whose state can be saved to
+    host memory (snapshot) and resumed (sw_score_job_resume)."""
+
+    def __init__(self, ctx: Context, handle, keep):
+        self.ctx, self.handle, self._keep = ctx, handle, keep
+        self.bands_done, self.bands_total, self.wave_bands = 0, None, None
+        self.run(0)
+
+    def run(self, bands: int = -1):
+        """Run up to `bands` more bands (-1: all that are left, 0: none);
+        returns (bands done, bands in total).  `wave_bands` is how many bands
+        the GPU runs at once: segments of whole waves add the least time."""
+        d, t, w = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(self.ctx, lib().sw_score_job_run(self.handle, int(bands), ctypes.byref(d), ctypes.byref(t),
+                                                ctypes.byref(w)))
+        self.bands_done, self.bands_total, self.wave_bands = d.value, t.value, w.value
+        return d.value, t.value
+
+    def snapshot(self) -> bytes:
+        n = ctypes.c_uint64()
+        st = lib().sw_score_job_snapshot(self.handle, None, 0, ctypes.byref(n))
+        if st not in (SW_OK, SW_ENOMEM):
+            _check(self.ctx, st)
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self.ctx, lib().sw_score_job_snapshot(self.handle, buf, n.value, ctypes.byref(n)))
+        return buf.raw[:n.value]
+
+    def result(self) -> Result:
+        res = _Result()
+        _check(self.ctx, lib().sw_score_job_result(self.handle, ctypes.byref(res)))
+        return _result(res)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sw_score_job_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _job_args(a, b, scheme, flags):
+    pa, n, da, ka = _seq(a)
+    pb, m, db, kb = _seq(b)
+    if da != db:
+        raise ValueError("a and b must both be host or both be device sequences")
+    if da:
+        flags |= SW_FLAG_DEVICE_INPUT
+    sch, keep = (scheme or DNA)._c()
+    return pa, n, pb, m, sch, flags, (ka, kb, keep)
+
+
+def sw_score_job_create(ctx: Context, a, b, scheme: Scheme | None = None, flags: int = 0) -> ScoreJob:
+    """A checkpointable score pass over (a, b); run it with ScoreJob.run."""
+    pa, n, pb, m, sch, flags, keep = _job_args(a, b, scheme, flags)
+    h = ctypes.c_void_p()
+    _check(ctx, lib().sw_score_job_create(ctx.handle, pa, n, pb, m, ctypes.byref(sch), flags, ctypes.byref(h)))
+    return ScoreJob(ctx, h, keep)
+
+
+def sw_score_job_resume(ctx: Context, a, b, snapshot: bytes, scheme: Scheme | None = None,
+                        flags: int = 0) -> ScoreJob:
+    """Rebuild a job from ScoreJob.snapshot() for the same sequences, scheme and flags."""
+    pa, n, pb, m, sch, flags, keep = _job_args(a, b, scheme, flags)
+    h = ctypes.c_void_p()
+    snap = ctypes.create_string_buffer(bytes(snapshot), len(snapshot))
+    _check(ctx, lib().sw_score_job_resume(ctx.handle, pa, n, pb, m, ctypes.byref(sch), flags, snap,
+                                          len(snapshot), ctypes.byref(h)))
+    return ScoreJob(ctx, h, keep)
 
 
 class Server:

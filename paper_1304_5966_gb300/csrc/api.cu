@@ -121,6 +121,79 @@ static int auto_rpt16(sw_ctx *ctx, const std::vector<FwdJob> &jobs, bool rel, co
     return 4;
 }
 
+void fwd_params(sw_ctx *ctx, const SchemeDev &sc, bool prune, const FwdProblem *dprobs, const int2 *dtk,
+                int64_t ntk, int32_t *ctrs, unsigned long long *dstats, FwdParams &P)
+{
+    std::memset(&P, 0, sizeof P);
+    P.probs = dprobs;
+    P.tickets = dtk;
+    P.ntickets = (int32_t)ntk;
+    P.ticket_ctr = ctrs;
+    P.err = ctrs + 1;
+    P.stats = dstats;
+    for (int x = 0; x < 8; ++x) {
+        P.prof_lo[x] = sc.prof_lo[x]; P.prof_hi[x] = sc.prof_hi[x];
+        P.prof_lo_t[x] = sc.prof_lo_t[x]; P.prof_hi_t[x] = sc.prof_hi_t[x];
+    }
+    P.go = sc.go; P.ge = sc.ge; P.max_sub = sc.max_sub;
+    P.slack = std::max(sc.go, -sc.min_sub);
+    P.prune = prune ? 1 : 0;
+    P.fault_band = ctx->opt.fault_band;
+    P.timeout_ns = (unsigned long long)ctx->opt.timeout_ms * 1000000ull;
+}
+
+void fwd_launch_shape(sw_ctx *ctx, const SchemeDev &sc, int64_t ntk, int rpt, bool lane16, bool rel, bool anch,
+                      int *ctas_out, int *cta_warps_out, bool *wide_out)
+{
+    const bool p2 = sc.alphabet > 4;
+    int ctas, cta_warps = 4;
+    // local pass with offset lanes and bands enough to fill every SM twice over:
+    // one CTA per SM, each scheduler on consecutive bands
+    const bool wide = lane16 && rel && !anch && ctx->opt.warps_per_sm <= 0 &&
+                      ntk >= 2 * (int64_t)ctx->sms * fwd16_cta_warps(rpt, true);
+    if (lane16) {
+        int per_sm = 1;
+        cta_warps = fwd16_cta_warps(rpt, wide);
+        if (fwd16_occupancy(rpt, rel, rel && anch, wide, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+        if (ctx->opt.warps_per_sm > 0) per_sm = std::max(1, std::min(per_sm, ctx->opt.warps_per_sm / 4));
+        ctas = per_sm * ctx->sms;
+    } else {
+        ctas = occupancy_ctas(ctx, rpt, p2);
+    }
+    ctas = (int)std::min<int64_t>(ctas, (ntk + cta_warps - 1) / cta_warps);
+    *ctas_out = ctas;
+    *cta_warps_out = cta_warps;
+    *wide_out = wide;
+}
+
+cudaError_t fwd_launch_pass(sw_ctx *ctx, const SchemeDev &sc, const FwdParams &P, int rpt, bool lane16, bool rel,
+                            bool anch, int *cta_warps_out, int64_t shape_ntk)
+{
+    int ctas = 0, cta_warps = 4;
+    bool wide = false;
+    fwd_launch_shape(ctx, sc, shape_ntk > 0 ? shape_ntk : P.ntickets, rpt, lane16, rel, anch, &ctas, &cta_warps,
+                     &wide);
+    if (cta_warps_out) *cta_warps_out = cta_warps;
+    return lane16 ? fwd16_launch(P, rpt, rel, rel && anch, wide, ctas, ctx->stream)
+                  : fwd_launch(P, rpt, sc.alphabet > 4, ctas, 128, ctx->stream);
+}
+
+void forward_plan(sw_ctx *ctx, const SchemeDev &sc, const FwdJob &job, bool allow16, bool *lane16, int *rpt)
+{
+    const std::vector<FwdJob> jobs(1, job);
+    const int opt = ctx->opt.rows_per_thread;
+    const bool rel_ok = allow16 && ctx->opt.forward_lanes != 32 && rel16_fits(sc, 4) &&
+                        (ctx->opt.forward_lanes == 16 || opt <= 0);
+    if (rel_ok) {
+        *lane16 = true;
+        *rpt = (ctx->opt.forward_lanes == 16 && fwd16_rpt_supported(opt) && rel16_fits(sc, opt))
+                   ? opt : auto_rpt16(ctx, jobs, true, sc);
+    } else {
+        *lane16 = false;
+        *rpt = fwd_rpt_supported(opt) ? opt : auto_rpt(ctx, jobs, sc.alphabet > 4);
+    }
+}
+
 static int run_forward_impl(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &jobs, bool prune,
                             int rpt, bool lane16, bool rel, std::vector<int4> &res, std::vector<int> *ovf,
                             sw_stats *stats, float *ms)
@@ -216,40 +289,10 @@ static int run_forward_impl(sw_ctx *ctx, const SchemeDev &sc, const std::vector<
     if ((e = fwd_init_launch(dprobs, np, hp.data(), 0, anch ? 0 : -sc.go, lane16 ? (rel && anch ? 2 : 1) : 0, s)))
         return set_cuda_error(ctx, e, "forward init");
     FwdParams P;
-    std::memset(&P, 0, sizeof P);
-    P.probs = dprobs;
-    P.tickets = dtk;
-    P.ntickets = (int32_t)ntk;
-    P.ticket_ctr = ctrs;
-    P.err = ctrs + 1;
-    P.stats = dstats;
-    for (int x = 0; x < 8; ++x) {
-        P.prof_lo[x] = sc.prof_lo[x]; P.prof_hi[x] = sc.prof_hi[x];
-        P.prof_lo_t[x] = sc.prof_lo_t[x]; P.prof_hi_t[x] = sc.prof_hi_t[x];
-    }
-    P.go = sc.go; P.ge = sc.ge; P.max_sub = sc.max_sub;
-    P.slack = std::max(sc.go, -sc.min_sub);
-    P.prune = prune ? 1 : 0;
-    P.fault_band = ctx->opt.fault_band;
-    P.timeout_ns = (unsigned long long)ctx->opt.timeout_ms * 1000000ull;
-    const bool p2 = sc.alphabet > 4;
-    int ctas, cta_warps = 4;
-    // local pass with offset lanes and bands enough to fill every SM twice over:
-    // one CTA per SM, each scheduler on consecutive bands
-    const bool wide = lane16 && rel && !anch && ctx->opt.warps_per_sm <= 0 &&
-                      ntk >= 2 * (int64_t)ctx->sms * fwd16_cta_warps(rpt, true);
-    if (lane16) {
-        int per_sm = 1;
-        cta_warps = fwd16_cta_warps(rpt, wide);
-        if (fwd16_occupancy(rpt, rel, rel && anch, wide, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
-        if (ctx->opt.warps_per_sm > 0) per_sm = std::max(1, std::min(per_sm, ctx->opt.warps_per_sm / 4));
-        ctas = per_sm * ctx->sms;
-    } else {
-        ctas = occupancy_ctas(ctx, rpt, p2);
-    }
-    ctas = (int)std::min<int64_t>(ctas, (ntk + cta_warps - 1) / cta_warps);
+    fwd_params(ctx, sc, prune, dprobs, dtk, ntk, ctrs, dstats, P);
+    int cta_warps = 4;
     cudaEventRecord(ctx->ev[0], s);
-    if ((e = lane16 ? fwd16_launch(P, rpt, rel, rel && anch, wide, ctas, s) : fwd_launch(P, rpt, p2, ctas, 128, s)))
+    if ((e = fwd_launch_pass(ctx, sc, P, rpt, lane16, rel, anch, &cta_warps)))
         return set_cuda_error(ctx, e, "forward launch");
     cudaEventRecord(ctx->ev[1], s);
     if ((e = fwd_reduce_launch(dprobs, np, dres, s))) return set_cuda_error(ctx, e, "forward reduce");

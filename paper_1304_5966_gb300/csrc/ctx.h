@@ -177,6 +177,22 @@ struct FwdJob {
 };
 int run_forward(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &jobs, bool prune,
                 int rpt, std::vector<int4> &res, sw_stats *stats, float *ms);
+// Kernel parameters of one forward launch over the problems dprobs[] and the
+// tickets dtk[0, ntk) (counters: ctrs[0] ticket, ctrs[1] error word)
+void fwd_params(sw_ctx *ctx, const SchemeDev &sc, bool prune, const FwdProblem *dprobs, const int2 *dtk,
+                int64_t ntk, int32_t *ctrs, unsigned long long *dstats, FwdParams &P);
+// launch shape of a forward pass over ntk tickets: CTAs, warps per CTA (one band
+// each at a time) and whether it is the one-CTA-per-SM layout
+void fwd_launch_shape(sw_ctx *ctx, const SchemeDev &sc, int64_t ntk, int rpt, bool lane16, bool rel, bool anch,
+                      int *ctas, int *cta_warps, bool *wide);
+// launches the forward kernel for P on the context's stream with the launch
+// shape the library uses (one CTA per SM for long local passes on offset
+// lanes), chosen for shape_ntk tickets (> 0; else P's own count)
+cudaError_t fwd_launch_pass(sw_ctx *ctx, const SchemeDev &sc, const FwdParams &P, int rpt, bool lane16, bool rel,
+                            bool anch, int *cta_warps, int64_t shape_ntk = -1);
+// lanes (int16x2 offset lanes or int32) and band height that run_forward starts
+// a single local problem with (int32 lanes only when allow16 is false)
+void forward_plan(sw_ctx *ctx, const SchemeDev &sc, const FwdJob &job, bool allow16, bool *lane16, int *rpt);
 int run_forward32(sw_ctx *ctx, const SchemeDev &sc, const std::vector<FwdJob> &jobs, bool prune,
                   int rpt, std::vector<int4> &res, sw_stats *stats, float *ms);
 
