@@ -272,7 +272,8 @@ def bench_checkpointed(sw, ctx, ta, tb, one_pass):
 
 
 def bench_small_pairs(sw, ctx, reps: int = 9):
-    """The 1 kbp pair (BASELINE config 1) and the 100 kbp pair (config 2):
+    """The 1,000 x ~1,000 pair (an 800-base mutated window of A in random
+    flanks) and the 100,000 x ~100,000 homologous pair with tandem repeats:
     median wall latency of sw_align and of sw_score per call (host inputs,
     results read back), and their GCUPS."""
     from gen import synth
