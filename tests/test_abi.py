@@ -69,3 +69,20 @@ def test_struct_layout_matches_header(tmp_path):
         assert int(got[f"{cname} size"]) == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert int(got[f"{cname} {f}"]) == getattr(py, f).offset, (cname, f)
+
+
+def test_batch_results_view_reads_every_field():
+    """The bulk numpy view over a result array reads score, coordinates, cell
+    count and strand at the C offsets (no GPU: results without CIGARs)."""
+    import paper_1304_5966_gb300 as sw
+    outs = (sw._Result * 3)()
+    for k in range(3):
+        outs[k].score, outs[k].a_begin, outs[k].a_end = 10 * k + 1, k, k + 5
+        outs[k].b_begin, outs[k].b_end, outs[k].strand = 2 * k, 2 * k + 7, k % 2
+        outs[k].stats.cells = 1000 + k
+    outs[0].stats.tuned, outs[0].stats.band_rows = 1, 1024
+    res = sw._batch_results(outs, 3)
+    assert [(r.score, r.a_begin, r.a_end, r.b_begin, r.b_end, r.strand) for r in res] == \
+        [(1, 0, 5, 0, 7, 0), (11, 1, 6, 2, 9, 1), (21, 2, 7, 4, 11, 0)]
+    assert res[0].stats["tuned"] == 1 and res[0].stats["band_rows"] == 1024 and res[0].cigar is None
+    assert res[1].stats == {"cells": 1001} and res[2].stats == {"cells": 1002}
